@@ -1,0 +1,193 @@
+"""numpy front end of the oracle library (TEST INFRASTRUCTURE ONLY).
+
+The C sources next to this file are compiled with gcc into ``_build/libk2ref.so``
+on first use (or by ``build()``), with -ffp-contract=off so that the only fused
+operations are the explicit ``fma`` calls of the paper's formulas.
+"""
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libk2ref.so")
+_SRC = [os.path.join(_HERE, f) for f in ("k2ref.c", "k2ref_body.inc", "k2ref_kog.c", "k2ref_bwd.c")]
+_lock = threading.Lock()
+_lib = None
+
+# Branch flags of info bits 8..15 (see k2ref.c)
+FLAGS = {"ext": 0x01, "fallback": 0x02, "swap": 0x04, "t2f2": 0x08, "t2f3": 0x10,
+         "t2inf": 0x20, "tpinf": 0x40, "psig": 0x80}
+
+
+def _sources():
+    return [s for s in _SRC if os.path.exists(s)]
+
+
+def build(force=False):
+    """Compile the oracle library (gcc, -O2, no fast-math, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = _sources()
+    if not force and os.path.exists(_SO):
+        so_t = os.path.getmtime(_SO)
+        if all(os.path.getmtime(s) <= so_t for s in srcs):
+            return _SO
+    cfiles = [s for s in srcs if s.endswith(".c")]
+    base = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    tmp = _SO + ".tmp.%d" % os.getpid()
+    cmd = base + ["-fopenmp"] + cfiles + ["-o", tmp, "-lm"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:  # retry without OpenMP (the oracle then runs on one thread)
+        cmd = base + cfiles + ["-o", tmp, "-lm"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + r.stderr)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_SO)
+            P, I64, I32, D, F = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_float
+            for sfx in ("d", "s"):
+                fn = getattr(L, "k2ref_gesvd2_" + sfx)
+                fn.argtypes = [I64, P, I64, P, I64, P, I64, P, I64, P, P, P, C.c_int]
+                fn.restype = C.c_int
+                fn = getattr(L, "k2ref_trsvd2_" + sfx)
+                fn.argtypes = [I64, P, P, P, P, I64, P, I64, P, I64, P, P, P, C.c_int]
+                fn.restype = C.c_int
+                T = D if sfx == "d" else F
+                fn = getattr(L, "k2ref_hypot_" + sfx)
+                fn.argtypes = [T, T]
+                fn.restype = T
+                getattr(L, "k2ref_trace_" + sfx).argtypes = [P, P, P]
+                getattr(L, "k2ref_efops_" + sfx).argtypes = [T, T, P, P]
+                fn = getattr(L, "k2ref_prec_" + sfx)
+                fn.argtypes = [I32, T, I32, T]
+                fn.restype = C.c_int
+                fn = getattr(L, "k2ref_effl_" + sfx)
+                fn.argtypes = [I32, T]
+                fn.restype = T
+                fn = getattr(L, "k2ref_ext_" + sfx)
+                fn.argtypes = [T, T, T, T, C.c_int, T, T]
+                fn.restype = T
+            L.k2ref_brute_sigma.argtypes = [P, P, P, P]
+            L.k2ref_dmetrics.argtypes = [I64, P, I64, P, I64, P, I64, P, P, I64, P]
+            _lib = L
+            _bind_extra(L)
+    return _lib
+
+
+def _bind_extra(L):
+    """Bindings of the n x n driver and the backward reference, when compiled in."""
+    P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    if hasattr(L, "k2ref_kogbet_d"):
+        for sfx in ("d", "s"):
+            fn = getattr(L, "k2ref_kogbet_" + sfx)
+            fn.argtypes = [I32, P, P, P, P, C.c_int, D, P, P]
+            fn.restype = C.c_int
+    if hasattr(L, "k2ref_gesvd2_bwd_d"):
+        L.k2ref_gesvd2_bwd_d.argtypes = [I64, P, P, P, I64, P, P, P, P, D]
+        L.k2ref_gesvd2_bwd_d.restype = C.c_int
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _dt(prec):
+    return np.float64 if prec == "d" else np.float32
+
+
+def gesvd2(G, prec="d", nthreads=1):
+    """SVD of a batch of 2x2 matrices given as SoA planes G[4, n] (g11, g21, g12, g22).
+
+    Returns a dict with U[4,n], V[4,n] (column-major planes), S[2,n] (rounded singular
+    values), Se[2,n] and Sf[2,n] (exact (e,f) form) and info[n]."""
+    T = _dt(prec)
+    G = np.ascontiguousarray(G, dtype=T)
+    n = G.shape[1]
+    U = np.empty((4, n), T); V = np.empty((4, n), T); S = np.empty((2, n), T)
+    Se = np.empty((2, n), np.int32); Sf = np.empty((2, n), T); info = np.empty(n, np.int32)
+    rc = getattr(lib(), "k2ref_gesvd2_" + prec)(n, _ptr(G), n, _ptr(U), n, _ptr(V), n, _ptr(S), n,
+                                                 _ptr(Se), _ptr(Sf), _ptr(info), int(nthreads))
+    if rc != 0:
+        raise ValueError("k2ref_gesvd2 returned %d" % rc)
+    return {"U": U, "V": V, "S": S, "Se": Se, "Sf": Sf, "info": info}
+
+
+def trsvd2(F, Gp, H, prec="d", nthreads=1):
+    """SVD of upper-triangular R = [[F, Gp], [0, H]] given as three planes."""
+    T = _dt(prec)
+    F = np.ascontiguousarray(F, dtype=T); Gp = np.ascontiguousarray(Gp, dtype=T)
+    H = np.ascontiguousarray(H, dtype=T)
+    n = F.shape[0]
+    U = np.empty((4, n), T); V = np.empty((4, n), T); S = np.empty((2, n), T)
+    Se = np.empty((2, n), np.int32); Sf = np.empty((2, n), T); info = np.empty(n, np.int32)
+    rc = getattr(lib(), "k2ref_trsvd2_" + prec)(n, _ptr(F), _ptr(Gp), _ptr(H), _ptr(U), n, _ptr(V), n,
+                                                 _ptr(S), n, _ptr(Se), _ptr(Sf), _ptr(info), int(nthreads))
+    if rc != 0:
+        raise ValueError("k2ref_trsvd2 returned %d" % rc)
+    return {"U": U, "V": V, "S": S, "Se": Se, "Sf": Sf, "info": info}
+
+
+def hypot(x, y, prec="d"):
+    """Correctly rounded hypot (Sect. 2)."""
+    return getattr(lib(), "k2ref_hypot_" + prec)(x, y)
+
+
+def trace(g, prec="d"):
+    """Intermediate values of one SVD: (r11, r12, r22, tan2phi, tanphi, tanpsi, tantheta), (t, t', s, flags)."""
+    T = _dt(prec)
+    g = np.ascontiguousarray(g, dtype=T)
+    tr = np.zeros(7, T); ints = np.zeros(4, np.int32)
+    getattr(lib(), "k2ref_trace_" + prec)(_ptr(g), _ptr(tr), _ptr(ints))
+    return tr, ints
+
+
+def efops(x, y, prec="d"):
+    """(e,f) of x*y, x/y, |x|(+)|y|, |x|(-)|y|, x, y by eqs. (binary), (plus), (minus)."""
+    T = _dt(prec)
+    e = np.zeros(6, np.int32); f = np.zeros(6, T)
+    getattr(lib(), "k2ref_efops_" + prec)(x, y, _ptr(e), _ptr(f))
+    return e, f
+
+
+def prec(ex, fx, ey, fy, p="d"):
+    return bool(getattr(lib(), "k2ref_prec_" + p)(ex, fx, ey, fy))
+
+
+def effl(e, f, prec="d"):
+    return getattr(lib(), "k2ref_effl_" + prec)(e, f)
+
+
+def ext(x1, y1, x2, y2, neg, d, sec, prec="d"):
+    """eq. (EXT): fl(fl(FL(FL(x1*y1 +- x2*y2)/d))/sec)."""
+    return getattr(lib(), "k2ref_ext_" + prec)(x1, y1, x2, y2, int(neg), d, sec)
+
+
+def brute_sigma(g):
+    """Closed-form singular values of one double 2x2 matrix in binary128 (not the method):
+    returns [(e, hi, lo), (e, hi, lo)] with sigma = (hi + lo) * 2^e."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    e = np.zeros(2, np.int32); hi = np.zeros(2); lo = np.zeros(2)
+    lib().k2ref_brute_sigma(_ptr(g), _ptr(e), _ptr(hi), _ptr(lo))
+    return [(int(e[k]), float(hi[k]), float(lo[k])) for k in range(2)]
+
+
+def dmetrics(G, out):
+    """re sigma1, re sigma2, re U, re V, re G (Sect. 4) in binary128 for double results."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    n = G.shape[1]
+    U = np.ascontiguousarray(out["U"], np.float64); V = np.ascontiguousarray(out["V"], np.float64)
+    Se = np.ascontiguousarray(out["Se"], np.int32); Sf = np.ascontiguousarray(out["Sf"], np.float64)
+    m = np.empty((5, n))
+    lib().k2ref_dmetrics(n, _ptr(G), n, _ptr(U), n, _ptr(V), n, _ptr(Se), _ptr(Sf), n, _ptr(m))
+    return m
