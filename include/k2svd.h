@@ -1,0 +1,111 @@
+/*
+ * libk2svd -- batched SVD of real 2x2 matrices by the enhanced Kogbetliantz method
+ * (V. Novakovic, "Arithmetical enhancements of the Kogbetliantz method for the SVD of
+ * order two", arXiv 2407.13116), on NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Sect. 1): G = U Sigma V^T with U, V orthogonal and sigma1 >= sigma2 >= 0.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * Pointers.  Every array argument is a DEVICE pointer (cudaMalloc'd or managed
+ *   memory), owned by the caller; the library never allocates, frees or keeps them.
+ *   Optional arrays are marked "nullable" and are skipped when NULL.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Calls are asynchronous and stream-ordered; a return value of 0 means
+ *   the work was enqueued.  Kernel faults surface as CUDA errors on that stream.
+ * SoA planes.  A "k-plane array" X of leading dimension ld >= batch holds element
+ *   (plane j, matrix i) at X[j*ld + i].  2x2 matrices use 4 planes in column-major
+ *   element order (x11, x21, x12, x22); singular values use 2 planes (sigma1, sigma2).
+ * Precision.  The d-variants compute in IEEE binary64 with binary128 emulated
+ *   exactly where eq. (EXT) of Sect. 3.2.2 asks for a wider type; the s-variants in
+ *   binary32 with binary64 for eq. (EXT).  Every result is bitwise reproducible and
+ *   independent of the launch configuration (end of Sect. 3.3.2).
+ * Errors.  Return 0 on success; -i when argument i (1-based) is invalid, checked in
+ *   order, LAPACK style; K2SVD_ECUDA when a CUDA call failed (the CUDA error is left
+ *   for cudaGetLastError to report).  Per-matrix conditions go to `info` (below).
+ * Inputs must be finite (Sect. 2).  A matrix with a NaN or infinite element gets
+ *   info = -1 and NaN in all its outputs; the other matrices are unaffected.
+ */
+#ifndef K2SVD_H
+#define K2SVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define K2SVD_ECUDA (-1000)
+
+/* info bits per matrix (when info != NULL and the input is finite):
+ *   bits 0-3  zero-pattern type t of G (eq. (ts): 1 = g11, 2 = g21, 4 = g12, 8 = g22 non-zero)
+ *   bits 4-7  type t' after the prescaling (Sect. 3.1)
+ *   bits 8-15 branch flags: */
+#define K2SVD_INFO_EXT      (1 << 8)   /* one element of R by eq. (EXT) (Sect. 3.2.2)          */
+#define K2SVD_INFO_FALLBACK (1 << 9)   /* t'=15 with r12''=0 or r22''=0, finished as Sect. 3.1 */
+#define K2SVD_INFO_SWAP     (1 << 10)  /* r11 < r22: transpose-swap of eq. (RT)                */
+#define K2SVD_INFO_T2F2     (1 << 11)  /* tan(2 phi) by eq. (t2f'')                            */
+#define K2SVD_INFO_T2F3     (1 << 12)  /* tan(2 phi) by eq. (t2f''')                           */
+#define K2SVD_INFO_T2INF    (1 << 13)  /* tan(2 phi) = inf, tan(phi) = 1 (Alg. 1)              */
+#define K2SVD_INFO_TPINF    (1 << 14)  /* tan(psi) = inf, eq. (tp') (Alg. 2)                   */
+#define K2SVD_INFO_PSIG     (1 << 15)  /* singular values reordered by eq. (prec) (Alg. 2)     */
+
+/*
+ * k2svd_dgesvd2 / k2svd_sgesvd2 -- SVD of `batch` general real 2x2 matrices.
+ * Method: Sect. 3 phases 1-3: the prescaling of eqs. (eG), (s), (ts); the simple cases
+ * of Sect. 3.1; the URV factorization of Sect. 3.2 (eq. (QR15), (EXT)); the SVD of the
+ * triangular factor by Alg. 1 and Alg. 2 with a correctly rounded hypot; the left-vector
+ * heuristic of Sect. 3.3.2 (eqs. (p+t), (p-t), (tan+-), (UV)).
+ *
+ *   batch   number of matrices, >= 0 (0: nothing is launched)
+ *   G       4-plane input, ld = ldg (read only)
+ *   U, V    4-plane outputs (ld = ldu, ldv): G = U diag(S) V^T, U and V exactly
+ *           representable products of signed permutations and rotations, never Inf/NaN
+ *   S       2-plane output (ld = lds): sigma1 >= sigma2 >= 0 rounded once to the working
+ *           type (they may overflow to +Inf or underflow; see Se/Sf)
+ *   Se, Sf  nullable 2-plane outputs (ld = lds): the exact exponent-"mantissa" form
+ *           sigma_i = Sf_i * 2^Se_i with 1 <= Sf_i < 2 (or Sf_i = 0, Se_i = 0), which
+ *           never overflows or underflows (Sect. 3.3.2)
+ *   info    nullable, one int32 per matrix (bits above)
+ *   stream  cudaStream_t as void*
+ * Planes of different arrays must not overlap.  Argument order for error codes:
+ * 1 batch, 2 G, 3 ldg, 4 U, 5 ldu, 6 V, 7 ldv, 8 S, 9 lds.
+ */
+int k2svd_dgesvd2(int64_t batch, const double *G, int64_t ldg,
+                  double *U, int64_t ldu, double *V, int64_t ldv,
+                  double *S, int64_t lds, int32_t *Se, double *Sf,
+                  int32_t *info, void *stream);
+int k2svd_sgesvd2(int64_t batch, const float *G, int64_t ldg,
+                  float *U, int64_t ldu, float *V, int64_t ldv,
+                  float *S, int64_t lds, int32_t *Se, float *Sf,
+                  int32_t *info, void *stream);
+
+/*
+ * k2svd_dtrsvd2 / k2svd_strsvd2 -- SVD of `batch` upper-triangular matrices
+ * R = [[F, Gu], [0, H]] given as three planes (the xLASV2 argument shape, Sect. 1 and the
+ * remark before the three-phase outline of Sect. 3).  Any signs and zeros are allowed;
+ * the result equals k2svd_?gesvd2 on [[F, Gu], [0, H]] bit for bit, and phase 2 of
+ * Sect. 3.2.2 (the t'=15 URV) never runs.  Unlike xLASV2 the singular values are
+ * non-negative and the full U, V are returned.
+ * Argument order for error codes: 1 batch, 2 F, 3 Gu, 4 H, 5 U, 6 ldu, 7 V, 8 ldv, 9 S, 10 lds.
+ */
+int k2svd_dtrsvd2(int64_t batch, const double *F, const double *Gu, const double *H,
+                  double *U, int64_t ldu, double *V, int64_t ldv,
+                  double *S, int64_t lds, int32_t *Se, double *Sf,
+                  int32_t *info, void *stream);
+int k2svd_strsvd2(int64_t batch, const float *F, const float *Gu, const float *H,
+                  float *U, int64_t ldu, float *V, int64_t ldv,
+                  float *S, int64_t lds, int32_t *Se, float *Sf,
+                  int32_t *info, void *stream);
+
+/*
+ * k2svd_version -- library version as major*10000 + minor*100 + patch.
+ */
+int k2svd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* K2SVD_H */

@@ -106,6 +106,14 @@ static int bn_cmp(const bn_t *a, const bn_t *b)
     return 0;
 }
 
+/* Operation counters (per thread) for the algorithmic operation count of the method:
+ * additions/subtractions, multiplications, fmas, divisions, correctly rounded hypots and
+ * evaluations of eq. (EXT).  Exact power-of-two scalings, comparisons and sign changes
+ * are not counted. */
+enum { OP_ADD, OP_MUL, OP_FMA, OP_DIV, OP_HYP, OP_EXT, OP_N };
+static _Thread_local long long k2ref_ops_d[OP_N], k2ref_ops_s[OP_N];
+#define K2OP(k) ((void)(SFX(k2ref_ops)[k]++))
+
 /* ------------------------------------------------------------------------- */
 /* Double precision: p = 53, T = binary128.                                  */
 /* ------------------------------------------------------------------------- */
@@ -169,6 +177,13 @@ static int bn_cmp(const bn_t *a, const bn_t *b)
 #define WSQRT sqrt
 #define RBITS uint32_t
 #include "k2ref_body.inc"
+
+/* Read (and optionally reset) the calling thread's operation counters. */
+void k2ref_opcount(int prec_double, long long out[6], int reset)
+{
+    long long *c = prec_double ? k2ref_ops_d : k2ref_ops_s;
+    for (int k = 0; k < OP_N; ++k) { out[k] = c[k]; if (reset) c[k] = 0; }
+}
 
 /* ------------------------------------------------------------------------- */
 /* Brute-force reference (not the method): closed-form singular values of     */

@@ -79,6 +79,7 @@ def lib():
                 fn.argtypes = [T, T, T, T, C.c_int, T, T]
                 fn.restype = T
             L.k2ref_brute_sigma.argtypes = [P, P, P, P]
+            L.k2ref_opcount.argtypes = [C.c_int, P, C.c_int]
             L.k2ref_dmetrics.argtypes = [I64, P, I64, P, I64, P, I64, P, P, I64, P]
             _lib = L
             _bind_extra(L)
@@ -171,6 +172,25 @@ def effl(e, f, prec="d"):
 def ext(x1, y1, x2, y2, neg, d, sec, prec="d"):
     """eq. (EXT): fl(fl(FL(FL(x1*y1 +- x2*y2)/d))/sec)."""
     return getattr(lib(), "k2ref_ext_" + prec)(x1, y1, x2, y2, int(neg), d, sec)
+
+
+OPS = ("add", "mul", "fma", "div", "hypot", "ext")
+
+
+def opcount(G, prec="d", triangular=False):
+    """Mean algorithmic operation counts per matrix of the method on a batch (one thread):
+    {add, mul, fma, div, hypot, ext} (exact scalings, comparisons and sign changes excluded)."""
+    L = lib()
+    buf = np.zeros(6, np.int64)
+    L.k2ref_opcount(1 if prec == "d" else 0, _ptr(buf), 1)
+    if triangular:
+        trsvd2(G[0], G[1], G[2], prec, nthreads=1)
+        n = G.shape[1]
+    else:
+        gesvd2(G, prec, nthreads=1)
+        n = G.shape[1]
+    L.k2ref_opcount(1 if prec == "d" else 0, _ptr(buf), 1)
+    return {k: float(v) / n for k, v in zip(OPS, buf)}
 
 
 def brute_sigma(g):

@@ -1,0 +1,456 @@
+// Floating-point primitives of the enhanced Kogbetliantz 2x2 SVD (arXiv 2407.13116, Sect. 2)
+// for sm_103a.  Everything here is exact or correctly rounded (round to nearest, ties to
+// even, gradual underflow); the kernels are compiled with -ftz=false -prec-div=true
+// -prec-sqrt=true --fmad=false, so the only fused operations are explicit fma calls.
+//
+// GB300 has a narrow FP64 pipe (about 2 DFMA per clock per SM), so the exact steps that
+// do not need FP64 arithmetic -- exponent extraction, (e,f) renormalisation, power-of-two
+// scaling, the rounding decision of hypot and the binary128 emulation of eq. (EXT) -- run
+// on the integer pipes.
+#pragma once
+#include <cstdint>
+
+namespace k2 {
+
+typedef unsigned __int128 u128;
+
+constexpr uint64_t D_MANT = 0x000FFFFFFFFFFFFFull;
+constexpr uint64_t D_HID = 0x0010000000000000ull;
+constexpr uint64_t D_SIGN = 0x8000000000000000ull;
+constexpr uint32_t F_MANT = 0x007FFFFFu;
+constexpr uint32_t F_HID = 0x00800000u;
+constexpr uint32_t F_SIGN = 0x80000000u;
+
+__device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
+__device__ __forceinline__ double dfrom(uint64_t b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ uint32_t fbits(float x) { return (uint32_t)__float_as_uint(x); }
+__device__ __forceinline__ float ffrom(uint32_t b) { return __uint_as_float(b); }
+
+__device__ __forceinline__ int clz128(u128 x)
+{
+    uint64_t hi = (uint64_t)(x >> 64), lo = (uint64_t)x;
+    return hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+}
+
+// ---------------------------------------------------------------------------------------
+// Per-type traits: exponent/mantissa split, exact scaling, constants.
+// For x != 0 finite: e = floor(lg|x|) (also for subnormals) and f = x 2^-e, 1 <= |f| < 2.
+// ---------------------------------------------------------------------------------------
+template <typename T> struct fpt;
+
+template <> struct fpt<double> {
+    typedef uint64_t bits_t;
+    static constexpr int P = 53, EMU = -1022, ENU = 1023;
+    __device__ static __forceinline__ double eps() { return 0x1p-53; }
+    __device__ static __forceinline__ double nu() { return 0x1.fffffffffffffp1023; }
+    __device__ static __forceinline__ double mu() { return 0x1p-1022; }
+
+    // (e, f) of x != 0
+    __device__ static __forceinline__ void split(double x, int &e, double &f)
+    {
+        uint64_t b = dbits(x), m = b & D_MANT;
+        int E = (int)((b >> 52) & 0x7FF);
+        if (E == 0) {
+            int sh = __clzll((long long)m) - 11;
+            e = -1022 - sh;
+            m = (m << sh) & D_MANT;
+        } else {
+            e = E - 1023;
+        }
+        f = dfrom((b & D_SIGN) | (1023ull << 52) | m);
+    }
+    __device__ static __forceinline__ int expo(double x) { int e; double f; split(x, e, f); return e; }
+    // f * 2^e rounded once; f = 0 or 1 <= |f| < 2
+    __device__ static __forceinline__ double ldexp_rn(double f, int e)
+    {
+        if (f == 0.0) return f;
+        uint64_t b = dbits(f), keep = b & (D_SIGN | D_MANT);
+        if (e > 1023) return dfrom((b & D_SIGN) | (0x7FFull << 52));
+        if (e >= -1022) return dfrom(keep | ((uint64_t)(e + 1023) << 52));
+        if (e < -1100) return dfrom(b & D_SIGN);
+        // subnormal result: one rounding, by a product with a normal power of two
+        double y = dfrom(keep | ((uint64_t)(e + 600 + 1023) << 52));
+        return y * 0x1p-600;
+    }
+    // x 2^s rounded once, any finite x
+    __device__ static __forceinline__ double scale(double x, int s)
+    {
+        if (x == 0.0) return x;
+        int e; double f; split(x, e, f);
+        return ldexp_rn(f, e + s);
+    }
+};
+
+template <> struct fpt<float> {
+    typedef uint32_t bits_t;
+    static constexpr int P = 24, EMU = -126, ENU = 127;
+    __device__ static __forceinline__ float eps() { return 0x1p-24f; }
+    __device__ static __forceinline__ float nu() { return 0x1.fffffep127f; }
+    __device__ static __forceinline__ float mu() { return 0x1p-126f; }
+
+    __device__ static __forceinline__ void split(float x, int &e, float &f)
+    {
+        uint32_t b = fbits(x), m = b & F_MANT;
+        int E = (int)((b >> 23) & 0xFF);
+        if (E == 0) {
+            int sh = __clz((int)m) - 8;
+            e = -126 - sh;
+            m = (m << sh) & F_MANT;
+        } else {
+            e = E - 127;
+        }
+        f = ffrom((b & F_SIGN) | (127u << 23) | m);
+    }
+    __device__ static __forceinline__ int expo(float x) { int e; float f; split(x, e, f); return e; }
+    __device__ static __forceinline__ float ldexp_rn(float f, int e)
+    {
+        if (f == 0.0f) return f;
+        uint32_t b = fbits(f), keep = b & (F_SIGN | F_MANT);
+        if (e > 127) return ffrom((b & F_SIGN) | (0xFFu << 23));
+        if (e >= -126) return ffrom(keep | ((uint32_t)(e + 127) << 23));
+        if (e < -160) return ffrom(b & F_SIGN);
+        float y = ffrom(keep | ((uint32_t)(e + 64 + 127) << 23));
+        return y * 0x1p-64f;
+    }
+    __device__ static __forceinline__ float scale(float x, int s)
+    {
+        if (x == 0.0f) return x;
+        int e; float f; split(x, e, f);
+        return ldexp_rn(f, e + s);
+    }
+};
+
+// ---------------------------------------------------------------------------------------
+// Exponent-"mantissa" pairs (Sect. 2): w = f 2^e with 1 <= |f| < 2, or (0, 0).
+// ---------------------------------------------------------------------------------------
+template <typename T> struct ef { int e; T f; };
+
+template <typename T> __device__ __forceinline__ ef<T> ef_of(T x)
+{
+    ef<T> w;
+    if (x == T(0)) { w.e = 0; w.f = T(0); }
+    else fpt<T>::split(x, w.e, w.f);
+    return w;
+}
+template <typename T> __device__ __forceinline__ T ef_fl(ef<T> w) { return fpt<T>::ldexp_rn(w.f, w.e); }
+
+// eq. (binary): x (.) y; the mantissa product lies in [1,4)
+template <typename T> __device__ __forceinline__ ef<T> ef_mul(ef<T> x, ef<T> y)
+{
+    T z = x.f * y.f;
+    ef<T> w;
+    if (z == T(0)) { w.e = 0; w.f = T(0); return w; }
+    w.e = x.e + y.e;
+    if (fabs(z) >= T(2)) { z = z * T(0.5); w.e += 1; }
+    w.f = z;
+    return w;
+}
+// eq. (binary): x (/) y; the mantissa quotient lies in (1/2, 2)
+template <typename T> __device__ __forceinline__ ef<T> ef_div(ef<T> x, ef<T> y)
+{
+    T z = x.f / y.f;
+    ef<T> w;
+    if (z == T(0)) { w.e = 0; w.f = T(0); return w; }
+    w.e = x.e - y.e;
+    if (fabs(z) < T(1)) { z = z * T(2); w.e -= 1; }
+    w.f = z;
+    return w;
+}
+// eq. (unary): 2^c (.) x
+template <typename T> __device__ __forceinline__ ef<T> ef_pow2(int c, ef<T> x)
+{
+    if (x.f != T(0)) x.e += c;
+    return x;
+}
+// eq. (prec)
+template <typename T> __device__ __forceinline__ bool ef_prec(ef<T> x, ef<T> y)
+{
+    int sx = (x.f > T(0)) - (x.f < T(0)), sy = (y.f > T(0)) - (y.f < T(0));
+    if (sx != sy) return sx < sy;
+    return (x.e < y.e) || ((x.e == y.e) && (x.f < y.f));
+}
+// eq. (plus), x, y > 0 finite
+template <typename T> __device__ __forceinline__ ef<T> ef_plus(T x, T y)
+{
+    T z = x + y;
+    if (z <= fpt<T>::nu()) return ef_of(z);
+    z = x * T(0.5) + y * T(0.5);
+    ef<T> w = ef_of(z);
+    w.e += 1;
+    return w;
+}
+// eq. (minus), x, y > 0 finite; c = e_mu + p - 1 - min(e_x, e_y) (Lemma 2.4)
+template <typename T> __device__ __forceinline__ ef<T> ef_minus(T x, T y)
+{
+    ef<T> w;
+    if (x == y) { w.e = 0; w.f = T(0); return w; }
+    T z = x - y;
+    if (fabs(z) >= fpt<T>::mu()) return ef_of(z);
+    int ex = fpt<T>::expo(x), ey = fpt<T>::expo(y);
+    int c = fpt<T>::EMU + fpt<T>::P - 1 - (ex < ey ? ex : ey);
+    z = fpt<T>::scale(x, c) - fpt<T>::scale(y, c);
+    w = ef_of(z);
+    if (w.f != T(0)) w.e -= c;
+    return w;
+}
+
+// ---------------------------------------------------------------------------------------
+// Correctly rounded hypot (Sect. 2).  With a = max(|x|,|y|), b = min:
+//  * e_a - e_b >= (p+1)/2: b^2 < a ulp(a), so sqrt(a^2+b^2) lies strictly inside
+//    (a, a + ulp(a)/2) and rounds to a;
+//  * a subnormal: both are integers times the smallest subnormal q, the result is
+//    round(sqrt(A^2+B^2)) q (no ties: 4N is even, (2k+1)^2 odd);
+//  * otherwise a candidate r = sqrt(fma(a', a', b'*b')) of the operands scaled to a' in
+//    [1,2) is within two steps of the result; it is corrected by comparing the exact
+//    a'^2 + b'^2 with the squared midpoints to the neighbouring values, in integers
+//    (units 2^-110 for double, 2^-52 for float), ties to even.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double hypot_cr(double x, double y)
+{
+    double a = fabs(x), b = fabs(y);
+    if (a < b) { double t = a; a = b; b = t; }
+    if (!(a <= 0x1.fffffffffffffp1023)) return a + b;     // inf or nan
+    if (b == 0.0) return a;
+    uint64_t ab = dbits(a), bb = dbits(b);
+    int Ea = (int)(ab >> 52), Eb = (int)(bb >> 52);
+    uint64_t A = ab & D_MANT, B = bb & D_MANT;
+    int ea, eb;
+    if (Ea) { A |= D_HID; ea = Ea - 1023; } else { int sh = __clzll((long long)A) - 11; A <<= sh; ea = -1022 - sh; }
+    if (Eb) { B |= D_HID; eb = Eb - 1023; } else { int sh = __clzll((long long)B) - 11; B <<= sh; eb = -1022 - sh; }
+    if (ea - eb >= 27) return a;
+    if (Ea == 0) {
+        u128 N = (u128)ab * ab + (u128)bb * bb;                 // units of 2^-2148
+        double nd = __ull2double_rn((unsigned long long)(N >> 41)) * 0x1p41;
+        uint64_t q = (uint64_t)__double2ull_rn(sqrt(nd));
+        u128 N4 = N << 2;
+#pragma unroll 1
+        for (int it = 0; it < 4; ++it) {
+            u128 hi = (u128)(2 * q + 1) * (2 * q + 1);
+            if (hi < N4) { ++q; continue; }
+            u128 lo = (u128)(2 * q - 1) * (2 * q - 1);
+            if (q > 0 && lo > N4) { --q; continue; }
+            break;
+        }
+        return dfrom(q);                                       // q * 2^-1074, q < 2^53
+    }
+    double as = dfrom((1023ull << 52) | (A & D_MANT));
+    double bs = dfrom(((uint64_t)(eb - ea + 1023) << 52) | (B & D_MANT));
+    double r = sqrt(fma(as, as, bs * bs));
+    // exact a'^2 + b'^2 in units of 2^-110, with a sticky bit for truncated bits of b'^2
+    u128 X = ((u128)A * A) << 6;
+    u128 B2 = (u128)B * B;
+    int sh = 2 * (eb - ea) + 6;
+    bool sticky = false;
+    if (sh >= 0) X += B2 << sh;
+    else { int k = -sh; sticky = (B2 << (128 - k)) != 0; X += B2 >> k; }
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+        uint64_t rb = dbits(r);
+        int er = (int)(rb >> 52) - 1023;                       // 0 or 1
+        uint64_t R = (rb & D_MANT) | D_HID;
+        u128 Mhi = ((u128)(2 * R + 1) * (2 * R + 1)) << (2 * er + 4);
+        if (X > Mhi || (X == Mhi && sticky)) { r = dfrom(rb + 1); continue; }
+        if (X == Mhi) { if (R & 1) r = dfrom(rb + 1); break; }
+        u128 Mlo = (R == D_HID) ? (((u128)(4 * R - 1) * (4 * R - 1)) << (2 * er + 2))
+                                : (((u128)(2 * R - 1) * (2 * R - 1)) << (2 * er + 4));
+        if (X < Mlo) { r = dfrom(rb - 1); continue; }
+        if (X == Mlo && !sticky && (R & 1)) r = dfrom(rb - 1);
+        break;
+    }
+    uint64_t rb = dbits(r);
+    int E = (int)(rb >> 52) + ea;                              // biased exponent of the result
+    if (E >= 2047) return dfrom(0x7FFull << 52);
+    return dfrom(((uint64_t)E << 52) | (rb & D_MANT));
+}
+
+__device__ __forceinline__ float hypot_cr(float x, float y)
+{
+    float a = fabsf(x), b = fabsf(y);
+    if (a < b) { float t = a; a = b; b = t; }
+    if (!(a <= 0x1.fffffep127f)) return a + b;
+    if (b == 0.0f) return a;
+    uint32_t ab = fbits(a), bb = fbits(b);
+    int Ea = (int)(ab >> 23), Eb = (int)(bb >> 23);
+    uint32_t A = ab & F_MANT, B = bb & F_MANT;
+    int ea, eb;
+    if (Ea) { A |= F_HID; ea = Ea - 127; } else { int sh = __clz((int)A) - 8; A <<= sh; ea = -126 - sh; }
+    if (Eb) { B |= F_HID; eb = Eb - 127; } else { int sh = __clz((int)B) - 8; B <<= sh; eb = -126 - sh; }
+    if (ea - eb >= 13) return a;
+    if (Ea == 0) {
+        uint64_t N = (uint64_t)ab * ab + (uint64_t)bb * bb;    // units of 2^-298
+        uint32_t q = (uint32_t)__float2uint_rn(sqrtf(__ull2float_rn(N)));
+        uint64_t N4 = N << 2;
+#pragma unroll 1
+        for (int it = 0; it < 4; ++it) {
+            uint64_t hi = (uint64_t)(2 * q + 1) * (2 * q + 1);
+            if (hi < N4) { ++q; continue; }
+            uint64_t lo = (uint64_t)(2 * q - 1) * (2 * q - 1);
+            if (q > 0 && lo > N4) { --q; continue; }
+            break;
+        }
+        return ffrom(q);
+    }
+    float as = ffrom((127u << 23) | (A & F_MANT));
+    float bs = ffrom(((uint32_t)(eb - ea + 127) << 23) | (B & F_MANT));
+    float r = sqrtf(fmaf(as, as, bs * bs));
+    uint64_t X = ((uint64_t)A * A) << 6;                       // units of 2^-52
+    uint64_t B2 = (uint64_t)B * B;
+    int sh = 2 * (eb - ea) + 6;
+    bool sticky = false;
+    if (sh >= 0) X += B2 << sh;
+    else { int k = -sh; sticky = (B2 << (64 - k)) != 0; X += B2 >> k; }
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+        uint32_t rb = fbits(r);
+        int er = (int)(rb >> 23) - 127;
+        uint64_t R = (rb & F_MANT) | F_HID;
+        uint64_t Mhi = ((2 * R + 1) * (2 * R + 1)) << (2 * er + 4);
+        if (X > Mhi || (X == Mhi && sticky)) { r = ffrom(rb + 1); continue; }
+        if (X == Mhi) { if (R & 1) r = ffrom(rb + 1); break; }
+        uint64_t Mlo = (R == F_HID) ? (((4 * R - 1) * (4 * R - 1)) << (2 * er + 2))
+                                    : (((2 * R - 1) * (2 * R - 1)) << (2 * er + 4));
+        if (X < Mlo) { r = ffrom(rb - 1); continue; }
+        if (X == Mlo && !sticky && (R & 1)) r = ffrom(rb - 1);
+        break;
+    }
+    uint32_t rb = fbits(r);
+    int E = (int)(rb >> 23) + ea;
+    if (E >= 255) return ffrom(0xFFu << 23);
+    return ffrom(((uint32_t)E << 23) | (rb & F_MANT));
+}
+
+// ---------------------------------------------------------------------------------------
+// eq. (EXT) for double: fl(FL(FL(x1 y1 +- x2 y2) / d)) with FL = IEEE binary128 rounding
+// (113 bits, ties to even) and fl = binary64 rounding with gradual underflow, emulated
+// exactly in integers.  The caller then divides by sec(theta) in double.  All operands
+// are finite and non-zero; d > 0.
+// ---------------------------------------------------------------------------------------
+struct q113 { u128 m; int e; bool neg; };   // value (-1)^neg * m * 2^e
+
+__device__ __forceinline__ void dmant(double x, uint64_t &M, int &e, bool &neg)
+{
+    uint64_t b = dbits(x);
+    neg = (b >> 63) != 0;
+    M = b & D_MANT;
+    int E = (int)((b >> 52) & 0x7FF);
+    if (E) { M |= D_HID; e = E - 1023 - 52; }
+    else { int sh = __clzll((long long)M) - 11; M <<= sh; e = -1022 - sh - 52; }
+}
+
+// round the non-negative integer value m * 2^e (+ a sticky fraction below bit 0) to 113 bits
+__device__ __forceinline__ void round113(u128 m, int e, bool sticky, u128 &M, int &E)
+{
+    int msb = 127 - clz128(m);
+    if (msb > 112) {
+        int k = msb - 112;
+        bool rbit = (m >> (k - 1)) & 1;
+        bool st = sticky || (k > 1 && (m << (129 - k)) != 0);
+        M = m >> k;
+        E = e + k;
+        if (rbit && (st || (M & 1))) {
+            M += 1;
+            if ((M >> 113) != 0) { M >>= 1; E += 1; }
+        }
+    } else {
+        M = m << (112 - msb);
+        E = e - (112 - msb);
+    }
+}
+
+__device__ __forceinline__ double ext_num_div(double x1, double y1, double x2, double y2, bool sub, double d)
+{
+    uint64_t a1, b1, a2, b2; int ea1, eb1, ea2, eb2; bool na1, nb1, na2, nb2;
+    dmant(x1, a1, ea1, na1); dmant(y1, b1, eb1, nb1);
+    dmant(x2, a2, ea2, na2); dmant(y2, b2, eb2, nb2);
+    // exact products, normalised with the top bit at position 126
+    u128 P1 = (u128)a1 * b1, P2 = (u128)a2 * b2;
+    int s1 = clz128(P1) - 1, s2 = clz128(P2) - 1;
+    P1 <<= s1; P2 <<= s2;
+    int f1 = ea1 + eb1 - s1, f2 = ea2 + eb2 - s2;
+    bool n1 = na1 ^ nb1, n2 = na2 ^ nb2 ^ sub;
+    // larger magnitude first
+    bool swap = (f2 > f1) || (f2 == f1 && P2 > P1);
+    u128 L = swap ? P2 : P1, S = swap ? P1 : P2;
+    int fL = swap ? f2 : f1, fS = swap ? f1 : f2;
+    bool nL = swap ? n2 : n1, nS = swap ? n1 : n2;
+    int dsh = fL - fS;
+    bool sticky;
+    u128 Sal;
+    if (dsh == 0) { Sal = S; sticky = false; }
+    else if (dsh >= 127) { Sal = 0; sticky = true; }
+    else { Sal = S >> dsh; sticky = (S << (128 - dsh)) != 0; }
+    u128 sum;
+    if (nL == nS) sum = L + Sal;
+    else sum = sticky ? (L - Sal - 1) : (L - Sal);
+    if (sum == 0 && !sticky) return 0.0;                    // exact cancellation: +0
+    u128 M1; int E1;
+    round113(sum, fL, sticky, M1, E1);                     // FL(x1 y1 +- x2 y2)
+    // FL(M1 2^E1 / d): integer quotient floor(M1 2^56 / Md), 116 or 117 bits, by 20-bit digits
+    uint64_t Md; int ed; bool nd;
+    dmant(d, Md, ed, nd);
+    uint64_t r = (uint64_t)(M1 >> 61);                      // top 52 bits of M1, below Md
+    u128 rest = (M1 & ((((u128)1) << 61) - 1)) << 56;      // the remaining 117 bits
+    const float mhi = __ull2float_rn(Md >> 29);             // exact, in [2^23, 2^24)
+    u128 q = 0;
+    int left = 117;
+#pragma unroll 1
+    while (left > 0) {
+        int w = left >= 20 ? 20 : left;
+        left -= w;
+        u128 rp = ((u128)r << w) | ((rest >> left) & ((((u128)1) << w) - 1));
+        float rhi = __ull2float_rn((uint64_t)(rp >> 49));    // exact: rp < 2^73
+        float qf = __fmul_rn(__fdiv_rn(rhi, mhi), 1048576.0f);
+        uint64_t qd = (uint64_t)qf;
+        if (qd > (1ull << w)) qd = 1ull << w;
+        u128 prod = (u128)qd * Md;
+#pragma unroll 1
+        while (prod > rp) { --qd; prod -= Md; }
+        u128 rr = rp - prod;
+#pragma unroll 1
+        while (rr >= Md) { ++qd; rr -= Md; }
+        r = (uint64_t)rr;
+        q = (q << w) | qd;
+    }
+    // quotient value = (q + r/Md) 2^(E1 + 52 - ed_true - 56) with ed_true = ed + 52
+    u128 M2; int E2;
+    round113(q, E1 - 56 - ed, r != 0, M2, E2);
+    // fl: round the 113-bit value M2 2^E2 (M2 in [2^112, 2^113)) to double
+    int etrue = E2 + 112;
+    bool neg = nL;
+    if (etrue > 1023) return neg ? -__longlong_as_double(0x7FF0000000000000ll) : __longlong_as_double(0x7FF0000000000000ll);
+    int k = (etrue >= -1022) ? 60 : (-1074 - E2);          // bits of M2 below the binary64 quantum
+    if (k > 114) return neg ? -0.0 : 0.0;
+    uint64_t Mr;
+    if (k >= 113) {
+        // M2 < 2^113 <= 2^k: the result is 0 or the smallest subnormal
+        bool rbit = (k == 113);                             // bit k-1 = 112 is the leading 1
+        bool st = M2 != (((u128)1) << 112);                 // bits below the leading one
+        Mr = (rbit && st) ? 1 : 0;
+    } else {
+        bool rbit = (M2 >> (k - 1)) & 1;
+        bool st = (k > 1) && ((M2 << (129 - k)) != 0);
+        Mr = (uint64_t)(M2 >> k);
+        if (rbit && (st || (Mr & 1))) Mr += 1;
+    }
+    uint64_t bits;
+    if (etrue >= -1022) {
+        int Eb = etrue + 1023;
+        if ((Mr >> 53) != 0) { Mr >>= 1; Eb += 1; }
+        if (Eb >= 2047) bits = 0x7FFull << 52;
+        else bits = ((uint64_t)Eb << 52) | (Mr & D_MANT);
+    } else {
+        bits = Mr;                                          // subnormal (or 2^-1022 after a carry)
+    }
+    return dfrom(bits | (neg ? D_SIGN : 0));
+}
+
+// eq. (EXT) for float: the wide type is double, where the products of floats are exact
+__device__ __forceinline__ float ext_num_div(float x1, float y1, float x2, float y2, bool sub, float d)
+{
+    double p2 = (double)x2 * (double)y2;
+    double num = fma((double)x1, (double)y1, sub ? -p2 : p2);
+    double q = num / (double)d;
+    return __double2float_rn(q);
+}
+
+}  // namespace k2

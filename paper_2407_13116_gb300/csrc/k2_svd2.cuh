@@ -1,0 +1,372 @@
+// One 2x2 SVD by the enhanced Kogbetliantz method (arXiv 2407.13116, Sect. 3), as a device
+// function: one matrix per thread, everything in registers.
+//
+// Phases (Sect. 3): (1) zero-pattern type t and scale type from eq. (ts), prescaling by
+// eqs. (eG), (s); (2) the simple cases of Sect. 3.1 or the URV of Sect. 3.2 (error-free for
+// t' ~ 13, fully pivoted with eq. (QR15)/(EXT) for t' = 15); (3) the SVD of R by Alg. 1 and
+// Alg. 2 after the transpose-swap of eq. (RT), the assembly of U and V (eqs. (UV15), (UV))
+// with the left-vector heuristic of eqs. (p+t), (p-t), (tan+-), and the backscaling.
+//
+// Readings of the text (each also stated where it is used):
+//  * class-9 types (0,1,2,4,6,8,9) are not scaled: s = 0 (Sect. 3.1, first sentence);
+//  * ties in magnitude comparisons never swap (strict "<");
+//  * sign(+-0) = +1; outputs -0 are returned as +0;
+//  * eq. (EXT) is used for the element with the essential subtraction only when tan(theta)
+//    is inexact, detected by fma(tan theta, g11''', -g21''') != 0 (Thm. 3.5);
+//  * P~ of eq. (RT) is the anti-identity (the printed identity is a typesetting error);
+//  * V = V_+ V-check P_sigma and U = S1 P_U S22 U(phi +- theta) S2 P_sigma (eq. (UV) with
+//    V_+ of eq. (UV15));
+//  * (cos, sin) of phi +- theta follow the direction of (D, N) with N, D the numerator and
+//    denominator of eq. (tan+-); a zero D or an overflowing N/D gives (0, sign N); the bold
+//    phi with an infinite tangent (tan psi = 0 after the swap) gives pi/2 +- theta exactly.
+#pragma once
+#include "k2_fp.cuh"
+
+namespace k2 {
+
+enum : int {
+    FL_EXT = 0x01, FL_FALLBACK = 0x02, FL_SWAP = 0x04, FL_T2F2 = 0x08,
+    FL_T2F3 = 0x10, FL_T2INF = 0x20, FL_TPINF = 0x40, FL_PSIG = 0x80
+};
+
+// class of each zero-pattern type, eq. (ts): 9, 3, 5, 13 or 15
+__device__ __forceinline__ int cls_of(int t)
+{
+    // bit k of these masks marks the types of a class
+    const unsigned c3 = (1u << 3) | (1u << 12), c5 = (1u << 5) | (1u << 10);
+    const unsigned c13 = (1u << 7) | (1u << 11) | (1u << 13) | (1u << 14);
+    unsigned b = 1u << t;
+    return (t == 15) ? 15 : (b & c13) ? 13 : (b & c3) ? 3 : (b & c5) ? 5 : 9;
+}
+
+template <typename T> struct m22 { T a11, a21, a12, a22; };   // column-major 2x2
+
+template <typename T> __device__ __forceinline__ void swap_rows(m22<T> &m)
+{
+    T t = m.a11; m.a11 = m.a21; m.a21 = t;
+    t = m.a12; m.a12 = m.a22; m.a22 = t;
+}
+template <typename T> __device__ __forceinline__ void swap_cols(m22<T> &m)
+{
+    T t = m.a11; m.a11 = m.a12; m.a12 = t;
+    t = m.a21; m.a21 = m.a22; m.a22 = t;
+}
+template <typename T> __device__ __forceinline__ void neg_row(m22<T> &m, int r)
+{
+    if (r == 0) { m.a11 = -m.a11; m.a12 = -m.a12; } else { m.a21 = -m.a21; m.a22 = -m.a22; }
+}
+template <typename T> __device__ __forceinline__ void neg_col(m22<T> &m, int c)
+{
+    if (c == 0) { m.a11 = -m.a11; m.a21 = -m.a21; } else { m.a12 = -m.a12; m.a22 = -m.a22; }
+}
+template <typename T> __device__ __forceinline__ m22<T> rot(T c, T s)     // [[c,-s],[s,c]]
+{
+    m22<T> m; m.a11 = c; m.a21 = s; m.a12 = -s; m.a22 = c; return m;
+}
+template <typename T> __device__ __forceinline__ m22<T> ident()
+{
+    m22<T> m; m.a11 = T(1); m.a21 = T(0); m.a12 = T(0); m.a22 = T(1); return m;
+}
+
+template <typename T> struct svd2_out {
+    m22<T> U, V;
+    ef<T> s1, s2;        // backscaled singular values, sigma1 >= sigma2
+    int info;
+};
+
+// sec = hypot(tan,1), cos = 1/sec, sin = tan/sec (Cor. 2.3, Lemma 3.2)
+template <typename T> __device__ __forceinline__ void cos_sin(T tn, T &c, T &s)
+{
+    T sec = hypot_cr(tn, T(1));
+    c = T(1) / sec;
+    s = tn / sec;
+}
+
+// Sect. 3.1, class 9: U = P_U diag(sign a, sign b), V = P_V, sigma' = (|a|, |b|)
+template <typename T>
+__device__ __forceinline__ void simple9(int tt, T g11, T g21, T g12, T g22, m22<T> &U, m22<T> &V, T &d1, T &d2)
+{
+    bool pu = false, pv = false;
+    T a = T(0), b = T(0);
+    switch (tt) {
+    case 1: a = g11; break;
+    case 2: pu = true; a = g21; break;
+    case 4: pv = true; a = g12; break;
+    case 8: pu = true; pv = true; a = g22; break;
+    case 9:
+        if (fabs(g11) < fabs(g22)) { pu = pv = true; a = g22; b = g11; } else { a = g11; b = g22; }
+        break;
+    case 6:
+        if (fabs(g12) < fabs(g21)) { pu = true; a = g21; b = g12; } else { pv = true; a = g12; b = g21; }
+        break;
+    default: break;
+    }
+    U = ident<T>();
+    if (pu) swap_rows(U);
+    if (a < T(0)) neg_col(U, 0);
+    if (b < T(0)) neg_col(U, 1);
+    V = ident<T>();
+    if (pv) swap_rows(V);
+    d1 = fabs(a); d2 = fabs(b);
+}
+
+// Sect. 3.1, classes 3 (one non-zero column) and 5 (one non-zero row): one Givens rotation
+template <typename T>
+__device__ __forceinline__ void simple35(int tt, T g11, T g21, T g12, T g22, m22<T> &U, m22<T> &V, T &d1)
+{
+    bool col = (tt == 3 || tt == 12);
+    bool p0;
+    T x0, x1;
+    if (col) { p0 = (tt == 12); x0 = p0 ? g12 : g11; x1 = p0 ? g22 : g21; }
+    else { p0 = (tt == 10); x0 = p0 ? g21 : g11; x1 = p0 ? g22 : g12; }
+    bool n0 = x0 < T(0), n1 = x1 < T(0);
+    T y0 = fabs(x0), y1 = fabs(x1);
+    bool p1 = y0 < y1;
+    T x = p1 ? y1 : y0, y = p1 ? y0 : y1;
+    T c, s;
+    cos_sin(y / x, c, s);
+    d1 = hypot_cr(x, y);
+    m22<T> R = rot(c, s);            // U_theta (column case) or V_theta (row case)
+    if (p1) swap_rows(R);
+    if (n0) neg_row(R, 0);
+    if (n1) neg_row(R, 1);
+    m22<T> P = ident<T>();
+    if (p0) swap_rows(P);
+    if (col) { U = R; V = P; } else { U = P; V = R; }
+}
+
+// State of the SVD of R~ (Sect. 3.3.1)
+template <typename T> struct tri_out {
+    bool swap, psig;
+    T tanphi, cphi, sphi, tanpsi, cpsi, spsi;
+    ef<T> s1, s2;
+};
+
+// Alg. 1 and Alg. 2 on R = [[r11, r12], [0, r22]] (all > 0), with the transpose-swap of eq. (RT)
+template <typename T>
+__device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int &flags)
+{
+    z.swap = r11 < r22;
+    T ra = z.swap ? r22 : r11, rb = r12, rc = z.swap ? r11 : r22;
+    if (z.swap) flags |= FL_SWAP;
+    ef<T> era = ef_of(ra), erb = ef_of(rb), erc = ef_of(rc);
+    T t2;
+    bool t2inf = false;
+    if (ra == rc) {                                        // eq. (t2f'')
+        t2 = (T(2) * rc) / rb;
+        flags |= FL_T2F2;
+    } else if (rb == rc) {                                 // eq. (t2f''')
+        t2 = ef_fl(ef_div(ef_mul(ef_pow2(1, erb), erc), ef_mul(era, era)));
+        flags |= FL_T2F3;
+    } else if (ra / rb < fpt<T>::eps()) {                 // eq. (t2f''), only for t' ~ 13
+        t2 = (T(2) * rc) / rb;
+        flags |= FL_T2F2;
+    } else {                                               // eq. (t2f')
+        T h = hypot_cr(ra, rb);
+        if (h == rc) { t2 = T(0); t2inf = true; }
+        else {
+            ef<T> s = ef_plus(h, rc), d = ef_minus(h, rc);
+            t2 = ef_fl(ef_div(ef_mul(ef_pow2(1, erb), erc), ef_mul(d, s)));
+        }
+    }
+    if (isinf(t2)) t2inf = true;
+    T tf;
+    if (t2inf) { tf = T(1); flags |= FL_T2INF; }
+    else tf = t2 / (T(1) + hypot_cr(t2, T(1)));           // eq. (tf)
+    T secf = hypot_cr(tf, T(1));
+    z.tanphi = tf;
+    z.cphi = T(1) / secf;
+    z.sphi = tf / secf;
+    // Alg. 2
+    T t = fma(rc, tf, rb);                                 // eq. (tp)
+    T tp = t / ra;
+    ef<T> s1, s2;
+    if (isinf(tp)) {                                       // eqs. (tp'), (s'')
+        ef<T> et = ef_of(t);
+        ef<T> ecos = ef_div(era, et);
+        z.cpsi = ef_fl(ecos);
+        z.spsi = T(1);
+        s1 = et;
+        s2 = ef_mul(erc, ecos);
+        flags |= FL_TPINF;
+    } else {                                               // eq. (s')
+        T secp = hypot_cr(tp, T(1));
+        z.cpsi = T(1) / secp;
+        z.spsi = tp / secp;
+        ef<T> sf = ef_div(ef_of(secf), ef_of(secp));
+        s1 = ef_div(era, sf);
+        s2 = ef_mul(erc, sf);
+    }
+    z.tanpsi = tp;
+    z.psig = ef_prec(s1, s2);                              // eq. (prec)
+    if (z.psig) { z.s1 = s2; z.s2 = s1; flags |= FL_PSIG; }
+    else { z.s1 = s1; z.s2 = s2; }
+}
+
+// U-check = P~ V_psi (swap) or U_phi, then P_sigma; V-check = P~ U_phi (swap) or V_psi, then P_sigma
+template <typename T> __device__ __forceinline__ m22<T> ucheck(const tri_out<T> &z)
+{
+    m22<T> m;
+    if (z.swap) { m.a11 = z.spsi; m.a21 = z.cpsi; m.a12 = z.cpsi; m.a22 = -z.spsi; }
+    else m = rot(z.cphi, z.sphi);
+    if (z.psig) swap_cols(m);
+    return m;
+}
+template <typename T> __device__ __forceinline__ m22<T> vcheck(const tri_out<T> &z)
+{
+    m22<T> m;
+    if (z.swap) { m.a11 = z.sphi; m.a21 = z.cphi; m.a12 = z.cphi; m.a22 = -z.sphi; }
+    else m = rot(z.cpsi, z.spsi);
+    if (z.psig) swap_cols(m);
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
+{
+    const int t = (g11 != T(0)) | ((g21 != T(0)) << 1) | ((g12 != T(0)) << 2) | ((g22 != T(0)) << 3);
+    const int cls = cls_of(t);
+    int s = 0, flags = 0;
+    if (cls != 9) {                                        // eqs. (eG), (s): class 9 is not scaled
+        int eG = INT_MIN;
+        if (g11 != T(0)) eG = max(eG, fpt<T>::expo(g11));
+        if (g21 != T(0)) eG = max(eG, fpt<T>::expo(g21));
+        if (g12 != T(0)) eG = max(eG, fpt<T>::expo(g12));
+        if (g22 != T(0)) eG = max(eG, fpt<T>::expo(g22));
+        s = fpt<T>::ENU - eG - (cls == 15 ? 2 : 1);
+        g11 = fpt<T>::scale(g11, s); g21 = fpt<T>::scale(g21, s);
+        g12 = fpt<T>::scale(g12, s); g22 = fpt<T>::scale(g22, s);
+    }
+    const int tp = (g11 != T(0)) | ((g21 != T(0)) << 1) | ((g12 != T(0)) << 2) | ((g22 != T(0)) << 3);
+    const int clsp = cls_of(tp);
+    bool simple = true;
+    T d1 = T(0), d2 = T(0);
+
+    if (clsp == 9) {
+        simple9(tp, g11, g21, g12, g22, o.U, o.V, d1, d2);
+    } else if (clsp == 3 || clsp == 5) {
+        simple35(tp, g11, g21, g12, g22, o.U, o.V, d1);
+    } else if (clsp == 13) {
+        // Sect. 3.2.1: permute to upper triangular, signs of row 1, column 2, row 2
+        simple = false;
+        bool pu = (tp == 11 || tp == 14), pv = (tp == 7 || tp == 11);
+        T a, b, d;
+        if (tp == 7) { a = g12; b = g11; d = g21; }
+        else if (tp == 11) { a = g22; b = g21; d = g11; }
+        else if (tp == 14) { a = g21; b = g22; d = g12; }
+        else { a = g11; b = g12; d = g22; }
+        bool n11 = a < T(0); a = fabs(a); if (n11) b = -b;
+        bool n12 = b < T(0); b = fabs(b); if (n12) d = -d;
+        bool n22 = d < T(0); d = fabs(d);
+        tri_out<T> z;
+        tri_svd(a, b, d, z, flags);
+        m22<T> U = ucheck(z);                              // U = P_U S11 S22 U-check
+        if (n11) neg_row(U, 0);
+        if (n22) neg_row(U, 1);
+        if (pu) swap_rows(U);
+        m22<T> V = vcheck(z);                              // V = P_V S12 V-check
+        if (n12) neg_row(V, 1);
+        if (pv) swap_rows(V);
+        o.U = U; o.V = V; o.s1 = z.s1; o.s2 = z.s2;
+    } else {
+        // Sect. 3.2.2: fully pivoted URV of a matrix without zeros
+        T w1 = hypot_cr(g11, g21), w2 = hypot_cr(g12, g22);
+        bool pv = w1 < w2;
+        if (pv) { T x = g11; g11 = g12; g12 = x; x = g21; g21 = g22; g22 = x; w1 = w2; }
+        bool n1a = g11 < T(0), n1b = g21 < T(0);            // S1
+        if (n1a) { g11 = -g11; g12 = -g12; }
+        if (n1b) { g21 = -g21; g22 = -g22; }
+        bool pu = g11 < g21;
+        if (pu) { T x = g11; g11 = g21; g21 = x; x = g12; g12 = g22; g22 = x; }
+        // eq. (QR15)
+        const T tth = g21 / g11;
+        const T secth = hypot_cr(tth, T(1));
+        T r11 = w1, r12, r22;
+        if (fma(tth, g11, -g21) == T(0)) {                // tan(theta) exact: Lemma 3.4
+            r12 = fma(g22, tth, g12) / secth;
+            r22 = fma(-g12, tth, g22) / secth;
+        } else if ((g12 < T(0)) == (g22 < T(0))) {         // Thm. 3.5: r22 by eq. (EXT)
+            r12 = fma(g22, tth, g12) / secth;
+            r22 = ext_num_div(g22, g11, g12, g21, true, g11) / secth;
+            flags |= FL_EXT;
+        } else {                                           // Thm. 3.5: r12 by eq. (EXT)
+            r22 = fma(-g12, tth, g22) / secth;
+            r12 = ext_num_div(g12, g11, g22, g21, false, g11) / secth;
+            flags |= FL_EXT;
+        }
+        if (r12 == T(0) || r22 == T(0)) {
+            // R'' of type 9 (or 1) or 5: finish as Sect. 3.1, G' = S1 P_U U_theta R'' P_V^T
+            flags |= FL_FALLBACK;
+            const T cth = T(1) / secth, sth = tth / secth;
+            m22<T> Ur, Vr;
+            if (r12 == T(0)) {
+                simple9<T>(r22 != T(0) ? 9 : 1, r11, T(0), T(0), r22, Ur, Vr, d1, d2);
+            } else {
+                simple35<T>(5, r11, T(0), r12, T(0), Ur, Vr, d1);
+                d2 = T(0);
+            }
+            // U_theta Ur, with Ur a signed permutation: pick and negate columns of U_theta
+            m22<T> M;
+            bool c0first = Ur.a11 != T(0);                 // non-zero of column 0 in row 0
+            T sg0 = c0first ? Ur.a11 : Ur.a21, sg1 = c0first ? Ur.a22 : Ur.a12;
+            T u0a = c0first ? cth : -sth, u0b = c0first ? sth : cth;   // U_theta column k0
+            T u1a = c0first ? -sth : cth, u1b = c0first ? cth : sth;   // U_theta column k1
+            M.a11 = sg0 < T(0) ? -u0a : u0a; M.a21 = sg0 < T(0) ? -u0b : u0b;
+            M.a12 = sg1 < T(0) ? -u1a : u1a; M.a22 = sg1 < T(0) ? -u1b : u1b;
+            if (pu) swap_rows(M);
+            if (n1a) neg_row(M, 0);
+            if (n1b) neg_row(M, 1);
+            o.U = M;
+            if (pv) swap_rows(Vr);
+            o.V = Vr;
+        } else {
+            simple = false;
+            bool n12 = r12 < T(0);
+            if (n12) { r12 = -r12; r22 = -r22; }            // R'' S12
+            bool n22 = r22 < T(0);
+            if (n22) r22 = -r22;                           // S22 R'
+            tri_out<T> z;
+            tri_svd(r11, r12, r22, z, flags);
+            m22<T> V = vcheck(z);                          // V = P_V S12 V-check
+            if (n12) neg_row(V, 1);
+            if (pv) swap_rows(V);
+            o.V = V;
+            // U = S1 P_U S22 U(phi +- theta) S2 P_sigma: eqs. (p+t), (p-t), (tan+-), (UV)
+            const bool plus = !n22;
+            const T tb = z.swap ? T(1) / z.tanpsi : z.tanphi;
+            T ca, sa;
+            if (isinf(tb)) {
+                const T cth = T(1) / secth, sth = tth / secth;
+                ca = plus ? -sth : sth; sa = cth;
+            } else {
+                const T N = plus ? tb + tth : tb - tth;
+                const T D = plus ? fma(-tb, tth, T(1)) : fma(tb, tth, T(1));
+                if (D == T(0)) { ca = T(0); sa = N < T(0) ? T(-1) : T(1); }
+                else {
+                    const T ta = N / D;
+                    if (isinf(ta)) { ca = T(0); sa = N < T(0) ? T(-1) : T(1); }
+                    else {
+                        T c0, s0;
+                        cos_sin(ta, c0, s0);
+                        if (D < T(0)) { ca = -c0; sa = -s0; } else { ca = c0; sa = s0; }
+                    }
+                }
+            }
+            m22<T> U = rot(ca, sa);
+            if (z.swap) neg_col(U, 1);                    // S2
+            if (n22) neg_row(U, 1);                        // S22
+            if (pu) swap_rows(U);                          // P_U
+            if (n1a) neg_row(U, 0);                        // S1
+            if (n1b) neg_row(U, 1);
+            if (z.psig) swap_cols(U);                      // P_sigma
+            o.U = U;
+            o.s1 = z.s1; o.s2 = z.s2;
+        }
+    }
+    if (simple) { o.s1 = ef_of(d1); o.s2 = ef_of(d2); }
+    o.s1 = ef_pow2(-s, o.s1);                              // Sect. 3.3.2: 2^-s (.) sigma~'
+    o.s2 = ef_pow2(-s, o.s2);
+    o.info = t | (tp << 4) | (flags << 8);
+}
+
+}  // namespace k2

@@ -160,12 +160,20 @@ def _as_real(B, bits, prec):
     return B.f64(bits) if prec == "d" else B.f32(bits)
 
 
-def general(n, seed, prec="d", kind="wide", i0=0, xp=None, device=None):
-    """Planes G[4, n] (g11, g21, g12, g22) of matrices i0 .. i0+n-1.
+def _indices(B, n, i0, idx, device):
+    if idx is None:
+        return B.arange(i0, i0 + n, device=device)
+    if B is NUMPY:
+        return np.asarray(idx, dtype=np.uint64)
+    return B.torch.as_tensor(np.asarray(idx, dtype=np.int64), device=device)
 
-    kind = "narrow" also applies the 25% triangular and 5% zero row/column patterns."""
+
+def general(n, seed, prec="d", kind="wide", i0=0, xp=None, device=None, idx=None):
+    """Planes G[4, n] (g11, g21, g12, g22) of matrices i0 .. i0+n-1 (or of the matrices with
+    the given indices).  kind = "narrow" also applies the 25% triangular and 5% zero
+    row/column patterns."""
     B = _backend(xp)
-    idx = B.arange(i0, i0 + n, device=device)
+    idx = _indices(B, n, i0, idx, device)
     planes = [_as_real(B, _elem_bits(B, seed, idx, k, prec, kind), prec) for k in range(4)]
     if kind == "narrow":
         d = splitmix(B, seed, idx * B.const(_PER) + B.const(12))
@@ -186,10 +194,10 @@ def general(n, seed, prec="d", kind="wide", i0=0, xp=None, device=None):
     return B.torch.stack(planes)
 
 
-def triangular(n, seed, prec="d", kind="wide", i0=0, xp=None, device=None):
+def triangular(n, seed, prec="d", kind="wide", i0=0, xp=None, device=None, idx=None):
     """(F, G, H) planes [3, n] of upper-triangular matrices [[F, G], [0, H]]."""
     B = _backend(xp)
-    idx = B.arange(i0, i0 + n, device=device)
+    idx = _indices(B, n, i0, idx, device)
     planes = [_as_real(B, _elem_bits(B, seed, idx, k, prec, kind), prec) for k in (0, 2, 3)]
     if B is NUMPY:
         return np.stack(planes)

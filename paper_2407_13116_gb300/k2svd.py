@@ -1,0 +1,163 @@
+"""Python binding of libk2svd (include/k2svd.h): argument marshalling only.
+
+Every function takes torch tensors that live on the current CUDA device, checks their
+dtype, device and layout, and calls the C ABI on torch's current stream.  All arithmetic
+runs in the library's kernels; there is no CPU path.  Loading fails with an error when
+the library has not been built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+_lib = None
+
+INFO_FLAGS = {"ext": 1 << 8, "fallback": 1 << 9, "swap": 1 << 10, "t2f2": 1 << 11,
+              "t2f3": 1 << 12, "t2inf": 1 << 13, "tpinf": 1 << 14, "psig": 1 << 15}
+
+
+class K2SVDError(RuntimeError):
+    pass
+
+
+def lib():
+    """The loaded libk2svd (ctypes.CDLL)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise K2SVDError("libk2svd is not built (%s missing); run __graft_entry__.build()" % path)
+        L = C.CDLL(path)
+        P, I64 = C.c_void_p, C.c_int64
+        for p in ("d", "s"):
+            f = getattr(L, "k2svd_%sgesvd2" % p)
+            f.argtypes = [I64, P, I64, P, I64, P, I64, P, I64, P, P, P, P]
+            f.restype = C.c_int
+            f = getattr(L, "k2svd_%strsvd2" % p)
+            f.argtypes = [I64, P, P, P, P, I64, P, I64, P, I64, P, P, P, P]
+            f.restype = C.c_int
+        _bind_extra(L)
+        _lib = L
+    return _lib
+
+
+def _bind_extra(L):
+    P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    if hasattr(L, "k2svd_dgesvd2_bwd"):
+        L.k2svd_dgesvd2_bwd.argtypes = [I64, P, P, P, I64, P, P, P, P, D, P]
+        L.k2svd_dgesvd2_bwd.restype = C.c_int
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _prefix(dtype):
+    if dtype == torch.float64:
+        return "d"
+    if dtype == torch.float32:
+        return "s"
+    raise K2SVDError("dtype must be float64 or float32, got %s" % dtype)
+
+
+def _check(t, name, dtype, device):
+    if t.dtype != dtype:
+        raise K2SVDError("%s: dtype %s, expected %s" % (name, t.dtype, dtype))
+    if t.device != device:
+        raise K2SVDError("%s: device %s, expected %s" % (name, t.device, device))
+    if not t.is_cuda:
+        raise K2SVDError("%s must be a CUDA tensor" % name)
+
+
+def _planes(t, k, name):
+    """(k, n) tensor with unit stride inside a plane; returns its leading dimension."""
+    if t.dim() != 2 or t.shape[0] != k:
+        raise K2SVDError("%s must have shape (%d, n), got %s" % (name, k, tuple(t.shape)))
+    if t.stride(1) != 1 and t.shape[1] > 1:
+        raise K2SVDError("%s: planes must be contiguous" % name)
+    return t.stride(0) if t.shape[0] > 1 else t.shape[1]
+
+
+def gesvd2(G, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_ef=False, want_info=True):
+    """SVD of the 2x2 matrices in the SoA planes G (4, n): (g11, g21, g12, g22).
+
+    Returns (U, V, S, Se, Sf, info) with U, V (4, n) column-major planes, S (2, n) rounded
+    singular values, Se/Sf (2, n) the exact (e,f) form (None unless requested) and info (n,)."""
+    p = _prefix(G.dtype)
+    dev = G.device
+    _check(G, "G", G.dtype, dev)
+    n = G.shape[1]
+    ldg = _planes(G, 4, "G")
+    U = torch.empty((4, n), dtype=G.dtype, device=dev) if U is None else U
+    V = torch.empty((4, n), dtype=G.dtype, device=dev) if V is None else V
+    S = torch.empty((2, n), dtype=G.dtype, device=dev) if S is None else S
+    if want_ef:
+        Se = torch.empty((2, n), dtype=torch.int32, device=dev) if Se is None else Se
+        Sf = torch.empty((2, n), dtype=G.dtype, device=dev) if Sf is None else Sf
+    if want_info and info is None:
+        info = torch.empty((n,), dtype=torch.int32, device=dev)
+    for t, nm, dt in ((U, "U", G.dtype), (V, "V", G.dtype), (S, "S", G.dtype)):
+        _check(t, nm, dt, dev)
+    ldu, ldv, lds = _planes(U, 4, "U"), _planes(V, 4, "V"), _planes(S, 2, "S")
+    if Se is not None:
+        _check(Se, "Se", torch.int32, dev)
+        if _planes(Se, 2, "Se") != lds:
+            raise K2SVDError("Se must have the leading dimension of S")
+    if Sf is not None:
+        _check(Sf, "Sf", G.dtype, dev)
+        if _planes(Sf, 2, "Sf") != lds:
+            raise K2SVDError("Sf must have the leading dimension of S")
+    if info is not None:
+        _check(info, "info", torch.int32, dev)
+    with torch.cuda.device(dev):
+        rc = getattr(lib(), "k2svd_%sgesvd2" % p)(n, _ptr(G), ldg, _ptr(U), ldu, _ptr(V), ldv, _ptr(S), lds,
+                                                  _ptr(Se), _ptr(Sf), _ptr(info), _stream())
+    if rc != 0:
+        raise K2SVDError("k2svd_%sgesvd2 returned %d" % (p, rc))
+    return U, V, S, Se, Sf, info
+
+
+def trsvd2(F, Gu, H, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_ef=False, want_info=True):
+    """SVD of the upper-triangular matrices [[F, Gu], [0, H]] given as three (n,) planes."""
+    p = _prefix(F.dtype)
+    dev = F.device
+    for t, nm in ((F, "F"), (Gu, "Gu"), (H, "H")):
+        _check(t, nm, F.dtype, dev)
+        if t.dim() != 1 or (t.numel() > 1 and t.stride(0) != 1):
+            raise K2SVDError("%s must be a contiguous vector" % nm)
+    n = F.shape[0]
+    if Gu.shape[0] != n or H.shape[0] != n:
+        raise K2SVDError("F, Gu, H must have the same length")
+    U = torch.empty((4, n), dtype=F.dtype, device=dev) if U is None else U
+    V = torch.empty((4, n), dtype=F.dtype, device=dev) if V is None else V
+    S = torch.empty((2, n), dtype=F.dtype, device=dev) if S is None else S
+    if want_ef:
+        Se = torch.empty((2, n), dtype=torch.int32, device=dev) if Se is None else Se
+        Sf = torch.empty((2, n), dtype=F.dtype, device=dev) if Sf is None else Sf
+    if want_info and info is None:
+        info = torch.empty((n,), dtype=torch.int32, device=dev)
+    ldu, ldv, lds = _planes(U, 4, "U"), _planes(V, 4, "V"), _planes(S, 2, "S")
+    with torch.cuda.device(dev):
+        rc = getattr(lib(), "k2svd_%strsvd2" % p)(n, _ptr(F), _ptr(Gu), _ptr(H), _ptr(U), ldu, _ptr(V), ldv,
+                                                  _ptr(S), lds, _ptr(Se), _ptr(Sf), _ptr(info), _stream())
+    if rc != 0:
+        raise K2SVDError("k2svd_%strsvd2 returned %d" % (p, rc))
+    return U, V, S, Se, Sf, info
+
+
+def to_planes(A):
+    """(..., 2, 2) matrices -> (4, n) SoA planes in column-major element order."""
+    a = A.reshape(-1, 2, 2)
+    return torch.stack([a[:, 0, 0], a[:, 1, 0], a[:, 0, 1], a[:, 1, 1]]).contiguous()
+
+
+def from_planes(X, shape):
+    """(4, n) planes -> (..., 2, 2)."""
+    m = torch.stack([torch.stack([X[0], X[2]], -1), torch.stack([X[1], X[3]], -1)], -2)
+    return m.reshape(*shape, 2, 2)
