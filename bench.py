@@ -1,0 +1,521 @@
+#!/usr/bin/env python
+"""Benchmark of libk2svd on GB300: FP64 2x2 SVDs/s on the wide-range workload, as a
+fraction of the FP64-pipe roofline, plus the FP32 variant and the end-to-end rate
+through the Python API with host buffers.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs the same per-GPU workload on its own GPU (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+
+Workload (one step, per GPU): 2^27 general matrices through k2svd_dgesvd2 plus 2^27
+upper-triangular matrices through k2svd_dtrsvd2, entries with exponents uniform over
+the normal range and 2% subnormal or near-overflow entries (paper_2407_13116_gb300/inputs.py).
+Inputs (7.5 GB) are larger than L2, so no L2 flush is needed between steps.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SEED = 0x240713116
+N_HALF_D = 1 << 27
+N_HALF_S = 1 << 28
+E2E_HALF = 1 << 25
+N_DIFF = 1 << 24
+E2E_CHUNK = 1 << 22
+METRIC = "FP64 2×2 SVDs/s & % of roofline; fwd+bwd/s; batched Kogbetliantz speedup"
+BYTES_GE = {"d": 112, "s": 56}          # in 4 T + out (4 U + 4 V + 2 S) T
+BYTES_TR = {"d": 104, "s": 52}          # in 3 T + out 10 T
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp32", action="store_true")
+    p.add_argument("--no-fwd-bwd", action="store_true")
+    p.add_argument("--profile-case", choices=["d", "s"], default=None,
+                   help="run a small case of the 2x2 kernels (for ncu captures) and exit")
+    p.add_argument("--profile-n", type=int, default=1 << 22)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; barrier and max-over-ranks timing only)
+# ----------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            import torch
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, x):
+        if self.world == 1:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            self.dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------------------
+# clock sampling during the timed region
+# ----------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({nm for r in rows for nm, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------------------
+# roofline bookkeeping
+# ----------------------------------------------------------------------------------------
+# DRAM traffic of the gesvd2 double kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of `python bench.py --profile-case d` (2^22 matrices), scaled by
+# the matrix count to a full 2^27-matrix launch.  Valid only for the kernel sources with
+# this hash; any change to them reports null until a new capture is taken.
+TRAFFIC_SRC_HASH = "ad1bb78823a8a59f"
+TRAFFIC_BYTES_PER_MATRIX = (135.570176e6 + 277.161728e6) / (1 << 22)
+KERNEL_SOURCES = ("k2_fp.cuh", "k2_svd2.cuh", "k2_gesvd2.cu")
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2407_13116_gb300", "csrc", f), "rb") as fh:
+            h.update(hashlib.sha256(fh.read()).hexdigest().encode() + b"  " + f.encode() + b"\n")
+    return h.hexdigest()[:16]
+
+
+def fp64_peak(clock_mhz):
+    """Nominal FP64 fma rate: 152 SMs x 2 DFMA per clock per SM (the sm_103 pipe rate
+    ncu reports as sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained) x clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * 2.0 * clock_mhz * 1e6
+
+
+def load_opcounts():
+    with open(os.path.join(ROOT, "tests", "golden", "opcounts.json")) as f:
+        return json.load(f)["workloads"]
+
+
+def slot_costs(c, rates, prec):
+    """FP64-pipe and FP32-pipe issue slots per matrix for the method's operations.
+
+    A division and a square root cost rate(fma)/rate(div) and rate(fma)/rate(sqrt) fma
+    slots of their pipe (measured); a correctly rounded hypot costs one multiplication,
+    one fma and one square root; eq. (EXT) is integer work for double (0 FP slots) and a
+    double multiplication, fma and division for float."""
+    if prec == "d":
+        wd, ws = rates["dfma"] / rates["ddiv"], rates["dfma"] / rates["dsqrt"]
+        fp64 = c["add"] + c["mul"] + c["fma"] + c["div"] * wd + c["hypot"] * (2 + ws)
+        return {"fp64": fp64, "fp32": 0.0}
+    wd, ws = rates["ffma"] / rates["fdiv"], rates["ffma"] / rates["fsqrt"]
+    fp32 = c["add"] + c["mul"] + c["fma"] + c["div"] * wd + c["hypot"] * (2 + ws)
+    fp64 = c["ext"] * (2 + rates["dfma"] / rates["ddiv"])
+    return {"fp64": fp64, "fp32": fp32}
+
+
+def probe_rates(L):
+    import ctypes as C
+    L.k2probe_rate.argtypes = [C.c_int, C.c_void_p]
+    L.k2probe_rate.restype = C.c_int
+    out = {}
+    for op, nm in enumerate(("dfma", "ddiv", "dsqrt", "ffma", "fdiv", "fsqrt")):
+        v = C.c_double(0)
+        rc = L.k2probe_rate(op, C.byref(v))
+        if rc != 0:
+            raise RuntimeError("k2probe_rate(%d) returned %d" % (op, rc))
+        out[nm] = v.value
+    return out
+
+
+# ----------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------
+def leg(prec, n_half, steps, warmup, dev, D, clocks_index=None):
+    """Time `steps` steps of gesvd2(n_half general) + trsvd2(n_half triangular)."""
+    import torch
+    from paper_2407_13116_gb300 import inputs as I
+    from paper_2407_13116_gb300 import k2svd
+    dt = torch.float64 if prec == "d" else torch.float32
+    G = I.general(n_half, SEED + 2, prec, "wide", xp="torch", device=dev)
+    T3 = I.triangular(n_half, SEED + 3, prec, "wide", xp="torch", device=dev)
+    F, Gu, H = T3[0], T3[1], T3[2]
+    Ug = torch.empty((4, n_half), dtype=dt, device=dev); Vg = torch.empty_like(Ug)
+    Sg = torch.empty((2, n_half), dtype=dt, device=dev)
+    Ut = torch.empty_like(Ug); Vt = torch.empty_like(Ug); St = torch.empty_like(Sg)
+    torch.cuda.synchronize()
+
+    def step():
+        k2svd.gesvd2(G, U=Ug, V=Vg, S=Sg, want_info=False)
+        k2svd.trsvd2(F, Gu, H, U=Ut, V=Vt, S=St, want_info=False)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(clocks_index) if clocks_index is not None else None
+    if clk:
+        clk.start()
+    D.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(steps):
+        ev[k][0].record(stream)
+        k2svd.gesvd2(G, U=Ug, V=Vg, S=Sg, want_info=False)
+        ev[k][1].record(stream)
+        k2svd.trsvd2(F, Gu, H, U=Ut, V=Vt, S=St, want_info=False)
+        ev[k][2].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    D.barrier()
+    clocks = clk.stop() if clk else None
+    ms = t0.elapsed_time(t1) / steps
+    ge_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    tr_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    del G, T3, F, Gu, H, Ug, Vg, Sg, Ut, Vt, St
+    torch.cuda.empty_cache()
+    return {"ms": ms, "ge_ms": ge_ms, "tr_ms": tr_ms, "clocks": clocks, "launches": 2 * steps}
+
+
+def fwd_bwd_leg(steps, warmup, dev, D):
+    """The differentiation workload: 2^24 FP64 matrices R(theta) diag(s1, s2) R(phi)^T; one step
+    is the forward (k2svd_dgesvd2) and the backward (k2svd_dgesvd2_bwd) with upstream
+    gradients dS, dU, dV ~ N(0,1)."""
+    import torch
+    from paper_2407_13116_gb300 import inputs as I
+    from paper_2407_13116_gb300 import k2svd
+    n = N_DIFF
+    G = torch.from_numpy(I.rotated(n, SEED + 3)[0]).to(dev)
+    gen = torch.Generator(device=dev).manual_seed(SEED + 3)
+    dS = torch.randn((2, n), dtype=torch.float64, device=dev, generator=gen)
+    dU = torch.randn((4, n), dtype=torch.float64, device=dev, generator=gen)
+    dV = torch.randn((4, n), dtype=torch.float64, device=dev, generator=gen)
+    U = torch.empty((4, n), dtype=torch.float64, device=dev); V = torch.empty_like(U)
+    S = torch.empty((2, n), dtype=torch.float64, device=dev); dG = torch.empty_like(U)
+    torch.cuda.synchronize()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record()
+        k2svd.gesvd2(G, U=U, V=V, S=S, want_info=False)
+        if ev:
+            ev[1].record()
+        k2svd.gesvd2_bwd(U, S, V, dS, dU, dV, dG=dG)
+        if ev:
+            ev[2].record()
+
+    for _ in range(warmup):
+        step()
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(steps)]
+    D.barrier()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        step(evs[k])
+    torch.cuda.synchronize()
+    D.barrier()
+    fwd = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    bwd = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    ms = D.max(fwd + bwd)
+    bwd_bytes = 192 * n
+    del G, dS, dU, dV, U, V, S, dG
+    torch.cuda.empty_cache()
+    return {"value": D.world * n / (ms / 1e3), "unit": "fwd+bwd/s", "matrices_per_gpu_per_step": n,
+            "fwd_ms": fwd, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd,
+            "bwd_roofline": {"bound": "hbm", "achieved": bwd_bytes / (bwd / 1e3) / 1e9, "peak": 6691.5,
+                             "unit": "GB/s", "frac": bwd_bytes / (bwd / 1e3) / 6691.5e9,
+                             "algorithmic_bytes": bwd_bytes},
+            "workload": "2^24 FP64 R(theta) diag(s1,s2) R(phi)^T, 10% near-equal singular values, upstream N(0,1)"}
+
+
+def e2e_leg(steps, warmup, dev):
+    """End to end through the Python API: pinned host inputs -> device -> kernels -> host
+    outputs, in chunks over two streams so that copies overlap the kernels."""
+    import torch
+    from paper_2407_13116_gb300 import inputs as I
+    from paper_2407_13116_gb300 import k2svd
+    n, c = E2E_HALF, E2E_CHUNK
+    nc = n // c
+    dt = torch.float64
+
+    def chunked(x):       # (k, n) -> (nc, k, c): every chunk one contiguous block
+        return x.reshape(x.shape[0], nc, c).permute(1, 0, 2).contiguous()
+
+    Gh = chunked(I.general(n, SEED + 2, "d", "wide", xp="torch", device=dev)).cpu().pin_memory()
+    Th = chunked(I.triangular(n, SEED + 3, "d", "wide", xp="torch", device=dev)).cpu().pin_memory()
+    outs = {k: torch.empty((nc, rows, c), dtype=dt, pin_memory=True) for k, rows in
+            (("Ug", 4), ("Vg", 4), ("Sg", 2), ("Ut", 4), ("Vt", 4), ("St", 2))}
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    bufs = []
+    for _ in range(2):
+        bufs.append({"G": torch.empty((4, c), dtype=dt, device=dev), "T": torch.empty((3, c), dtype=dt, device=dev),
+                     "U": torch.empty((4, c), dtype=dt, device=dev), "V": torch.empty((4, c), dtype=dt, device=dev),
+                     "S": torch.empty((2, c), dtype=dt, device=dev)})
+    main = torch.cuda.current_stream()
+
+    def step():
+        j = 0
+        for kind in ("g", "t"):
+            for q in range(nc):
+                st, b = streams[j % 2], bufs[j % 2]
+                j += 1
+                st.wait_stream(main)
+                with torch.cuda.stream(st):
+                    if kind == "g":
+                        b["G"].copy_(Gh[q], non_blocking=True)
+                        k2svd.gesvd2(b["G"], U=b["U"], V=b["V"], S=b["S"], want_info=False)
+                        U, V, S = outs["Ug"], outs["Vg"], outs["Sg"]
+                    else:
+                        b["T"].copy_(Th[q], non_blocking=True)
+                        k2svd.trsvd2(b["T"][0], b["T"][1], b["T"][2], U=b["U"], V=b["V"], S=b["S"], want_info=False)
+                        U, V, S = outs["Ut"], outs["Vt"], outs["St"]
+                    U[q].copy_(b["U"], non_blocking=True)
+                    V[q].copy_(b["V"], non_blocking=True)
+                    S[q].copy_(b["S"], non_blocking=True)
+                main.wait_stream(st)
+        torch.cuda.synchronize()
+
+    for _ in range(warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(steps):
+        step()
+    el = (time.perf_counter() - t) / steps
+    h2d = (4 + 3) * 8 * n
+    d2h = 2 * (4 + 4 + 2) * 8 * n
+    return {"value": 2 * n / el, "unit": "SVDs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "batch": 2 * n, "ms_per_step": el * 1e3}
+
+
+def cpu_baseline(seconds=10.0):
+    """The oracle (plain C, all host cores) on a bounded sample of the same workload."""
+    import oracle
+    from paper_2407_13116_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    probe = 1 << 14
+    Gs = I.general(probe, SEED + 2, "d", "wide")
+    Ts = I.triangular(probe, SEED + 3, "d", "wide")
+    t = time.perf_counter()
+    oracle.gesvd2(Gs, "d", nthreads=cores)
+    oracle.trsvd2(Ts[0], Ts[1], Ts[2], "d", nthreads=cores)
+    rate = 2 * probe / (time.perf_counter() - t)
+    m = int(min(max(rate * seconds / 2, probe), 1 << 23))
+    Gs = I.general(m, SEED + 2, "d", "wide")
+    Ts = I.triangular(m, SEED + 3, "d", "wide")
+    t = time.perf_counter()
+    oracle.gesvd2(Gs, "d", nthreads=cores)
+    oracle.trsvd2(Ts[0], Ts[1], Ts[2], "d", nthreads=cores)
+    el = time.perf_counter() - t
+    return {"value": 2 * m / el, "unit": "SVDs/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d general + %d triangular matrices of the wide-range FP64 workload, "
+                      "OpenMP over matrices on %d host threads, %.1f s" % (m, m, cores, el)}
+
+
+def run_ours(a):
+    import torch
+    D = Dist()
+    dev = torch.device("cuda", D.local)
+    torch.cuda.set_device(dev)
+    from paper_2407_13116_gb300 import build as B
+    B.build()
+    from paper_2407_13116_gb300 import k2svd
+    L = k2svd.lib()
+    rates = probe_rates(L)
+    oc = load_opcounts()
+    res = leg("d", N_HALF_D, a.steps, a.warmup, dev, D, clocks_index=D.local)
+    ms = D.max(res["ms"])
+    value = D.world * 2 * N_HALF_D / (ms / 1e3)
+    cost_ge = slot_costs(oc["wide_d_gesvd2"], rates, "d")["fp64"]
+    cost_tr = slot_costs(oc["wide_d_trsvd2"], rates, "d")["fp64"]
+    ach = N_HALF_D * cost_ge / (res["ge_ms"] / 1e3)
+    clk_mhz = (res["clocks"] or {}).get("sm_mhz") or 2070.0
+    peak = fp64_peak(clk_mhz)
+    roof_step = 2 * N_HALF_D / ((N_HALF_D * (cost_ge + cost_tr)) / peak)
+    traffic = TRAFFIC_BYTES_PER_MATRIX * N_HALF_D if kernel_hash() == TRAFFIC_SRC_HASH else None
+    roofline = {"bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9,
+                "unit": "G FP64-pipe op/s", "frac": ach / peak, "traffic": traffic,
+                "kernel": "svd2_kernel<double,false> (k2svd_dgesvd2)",
+                "kernel_ms": res["ge_ms"], "ops_per_matrix": cost_ge,
+                "algorithmic_bytes": BYTES_GE["d"] * N_HALF_D,
+                "peak_source": "nominal: SMs x 2 DFMA/clk x median SM clock %.0f MHz during the timed region; "
+                               "live probe reached %.3g DFMA/s; divide %.2f, sqrt %.2f fma slots (probe)" % (
+                                   clk_mhz, rates["dfma"], rates["dfma"] / rates["ddiv"], rates["dfma"] / rates["dsqrt"]),
+                "step_frac": value / D.world / roof_step,
+                "hbm_bound_svds_per_s": 1e9 * 6691.5 / ((BYTES_GE["d"] + BYTES_TR["d"]) / 2)}
+    out = {"metric": METRIC, "value": value, "unit": "SVDs/s", "n_gpus": D.world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "wide-range FP64 2x2 SVD: 2^27 general (k2svd_dgesvd2) + 2^27 upper-triangular "
+                                  "(k2svd_dtrsvd2) per GPU, exponents uniform in [-1021,1021], 2% subnormal or "
+                                  "near-overflow entries, SoA planes",
+                      "matrices_per_gpu_per_step": 2 * N_HALF_D, "l2": "inputs (7.5 GB) larger than L2",
+                      "parallelism": "replicas (weak scaling, no collective)"},
+           "clocks": res["clocks"], "gpu_launches": res["launches"], "roofline": roofline,
+           "pipe_rates": rates}
+    if not a.no_fp32:
+        rs = leg("s", N_HALF_S, a.steps, a.warmup, dev, D)
+        mss = D.max(rs["ms"])
+        cs_ge = slot_costs(oc["wide_s_gesvd2"], rates, "s")
+        cs_tr = slot_costs(oc["wide_s_trsvd2"], rates, "s")
+        roof32 = 2 / ((cs_ge["fp32"] + cs_tr["fp32"]) / rates["ffma"])
+        roof64 = 2 / ((cs_ge["fp64"] + cs_tr["fp64"]) / rates["dfma"])
+        roofhbm = 2 / ((BYTES_GE["s"] + BYTES_TR["s"]) / 6691.5e9)
+        vs = D.world * 2 * N_HALF_S / (mss / 1e3)
+        out["fp32"] = {"value": vs, "unit": "SVDs/s", "ms_per_step": mss, "matrices_per_gpu_per_step": 2 * N_HALF_S,
+                       "roofline_svds_per_s": {"fp32_pipe": roof32, "fp64_pipe": roof64, "hbm": roofhbm},
+                       "frac_of_min_roofline": vs / D.world / min(roof32, roof64, roofhbm),
+                       "gesvd2_ms": rs["ge_ms"], "trsvd2_ms": rs["tr_ms"]}
+    if not a.no_fwd_bwd:
+        out["fwd_bwd"] = fwd_bwd_leg(a.steps, a.warmup, dev, D)
+    if D.world == 1 and not a.no_e2e:
+        out["e2e"] = e2e_leg(max(2, a.steps // 3), 1, dev)
+    if D.rank == 0 and D.world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    D.close()
+    if D.rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------------------
+# reference arm: the oracle (the paper has no code; its CPU restatement is the reference)
+# ----------------------------------------------------------------------------------------
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2407_13116_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    m = 1 << 17
+    Gs = I.general(m, SEED + 2, "d", "wide")
+    Ts = I.triangular(m, SEED + 3, "d", "wide")
+
+    def step():
+        oracle.gesvd2(Gs, "d", nthreads=cores)
+        oracle.trsvd2(Ts[0], Ts[1], Ts[2], "d", nthreads=cores)
+
+    for _ in range(a.warmup):
+        step()
+    ts = []
+    for _ in range(a.steps):
+        t = time.perf_counter()
+        step()
+        ts.append(time.perf_counter() - t)
+    el = statistics.mean(ts)
+    value = 2 * m / el
+    sample = "first %d general + %d triangular matrices of the wide-range FP64 workload per step" % (m, m)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "SVDs/s", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": el * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "wide-range FP64 2x2 SVD (oracle, plain C on the host cores)",
+                      "matrices_per_step": 2 * m, "parallelism": "OpenMP over matrices"},
+           "cpu_baseline": {"value": value, "unit": "SVDs/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "SVDs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def profile_case(a):
+    """A few launches of each 2x2 kernel on a small batch of the wide-range workload
+    (2^22 matrices by default: 470 MB of inputs and outputs in double, above L2)."""
+    import torch
+    from paper_2407_13116_gb300 import inputs as I
+    from paper_2407_13116_gb300 import k2svd
+    dev = torch.device("cuda", 0)
+    n = a.profile_n
+    G = I.general(n, SEED + 2, a.profile_case, "wide", xp="torch", device=dev)
+    T3 = I.triangular(n, SEED + 3, a.profile_case, "wide", xp="torch", device=dev)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        k2svd.gesvd2(G, want_info=False)
+        k2svd.trsvd2(T3[0], T3[1], T3[2], want_info=False)
+    torch.cuda.synchronize()
+    print("profile case %s n=%d done" % (a.profile_case, n))
+
+
+def main():
+    a = parse()
+    if a.profile_case:
+        profile_case(a)
+        return
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

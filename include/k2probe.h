@@ -1,0 +1,28 @@
+/*
+ * k2probe -- pipe-throughput probes used to measure the roofline denominators of the
+ * libk2svd kernels on the device at hand.  They are measurement helpers, not part of the
+ * method; the paper has no counterpart.
+ *
+ * k2probe_rate: runs a fixed arithmetic loop of one operation kind on every SM and returns
+ * the sustained rate in operations per second in *rate.  Enough independent chains are in
+ * flight per thread to hide latency, so the result is the issue-limited throughput.
+ *   op   0 = FP64 fma, 1 = FP64 division, 2 = FP64 square root,
+ *        3 = FP32 fma, 4 = FP32 division, 5 = FP32 square root
+ *   rate host pointer, receives operations per second
+ * Returns 0, -1 for an unknown op, K2SVD_ECUDA (-1000) when a CUDA call failed.  Allocates
+ * and frees a small device buffer; synchronizes the device.
+ */
+#ifndef K2PROBE_H
+#define K2PROBE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+int k2probe_rate(int op, double *rate);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* K2PROBE_H */

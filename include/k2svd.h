@@ -100,6 +100,36 @@ int k2svd_strsvd2(int64_t batch, const float *F, const float *Gu, const float *H
                   int32_t *info, void *stream);
 
 /*
+ * k2svd_dgesvd2_bwd / k2svd_sgesvd2_bwd -- adjoint (backward) of the batched 2x2 SVD.
+ * The paper has no backward; this is the standard adjoint of a square SVD G = U S V^T
+ * with distinct singular values, with a gap threshold for near-equal ones:
+ *   J = U^T dU, K = V^T dV, a = J12 - J21, b = K12 - K21,
+ *   F12 = -1 / (max(s1 - s2, gap_rtol * s1) * (s1 + s2))  (F12 = 0 when s1 = 0),
+ *   M = [[dS1, F12 (a s2 + b s1)], [F12 (a s1 + b s2), dS2]],   dG = U M V^T.
+ * It is evaluated after scaling s1, s2 by the power of two that brings s1 into [1, 2),
+ * so that no intermediate overflows or underflows for any representable s1 > 0.
+ *
+ *   batch    number of matrices, >= 0
+ *   U, V     4-plane outputs of k2svd_?gesvd2 (read only)
+ *   S        2-plane singular values of k2svd_?gesvd2 (read only)
+ *   ld       leading dimension of every plane array of this call, >= batch
+ *   dS       nullable 2-plane upstream gradient of S (NULL = zero)
+ *   dU, dV   nullable 4-plane upstream gradients of U and V (NULL = zero)
+ *   dG       4-plane output, the gradient with respect to G (column-major planes)
+ *   gap_rtol relative gap threshold tau >= 0 (1e-10 is a good default); pairs with
+ *            s1 - s2 < tau s1 use tau s1 in place of the gap
+ *   stream   cudaStream_t as void*
+ * Argument order for error codes: 1 batch, 2 U, 3 S, 4 V, 5 ld, 9 dG, 10 gap_rtol.
+ * Non-finite inputs give non-finite outputs for that matrix only.
+ */
+int k2svd_dgesvd2_bwd(int64_t batch, const double *U, const double *S, const double *V, int64_t ld,
+                      const double *dS, const double *dU, const double *dV, double *dG,
+                      double gap_rtol, void *stream);
+int k2svd_sgesvd2_bwd(int64_t batch, const float *U, const float *S, const float *V, int64_t ld,
+                      const float *dS, const float *dU, const float *dV, float *dG,
+                      float gap_rtol, void *stream);
+
+/*
  * k2svd_version -- library version as major*10000 + minor*100 + patch.
  */
 int k2svd_version(void);

@@ -89,11 +89,10 @@ def lib():
 def _bind_extra(L):
     """Bindings of the n x n driver and the backward reference, when compiled in."""
     P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
-    if hasattr(L, "k2ref_kogbet_d"):
-        for sfx in ("d", "s"):
-            fn = getattr(L, "k2ref_kogbet_" + sfx)
-            fn.argtypes = [I32, P, P, P, P, C.c_int, D, P, P]
-            fn.restype = C.c_int
+    for sfx in ("d", "s"):
+        fn = getattr(L, "k2ref_kogbet_" + sfx)
+        fn.argtypes = [I32, P, P, P, P, C.c_int, D, P, P]
+        fn.restype = C.c_int
     if hasattr(L, "k2ref_gesvd2_bwd_d"):
         L.k2ref_gesvd2_bwd_d.argtypes = [I64, P, P, P, I64, P, P, P, P, D]
         L.k2ref_gesvd2_bwd_d.restype = C.c_int
@@ -191,6 +190,36 @@ def opcount(G, prec="d", triangular=False):
         n = G.shape[1]
     L.k2ref_opcount(1 if prec == "d" else 0, _ptr(buf), 1)
     return {k: float(v) / n for k, v in zip(OPS, buf)}
+
+
+def gesvd2_bwd(U, S, V, dS=None, dU=None, dV=None, tau=1e-10):
+    """Analytic adjoint of the batched 2x2 SVD in binary128 (double in and out):
+    dG (4, n) from U, V (4, n), S (2, n) and the optional upstream gradients."""
+    U = np.ascontiguousarray(U, np.float64); V = np.ascontiguousarray(V, np.float64)
+    S = np.ascontiguousarray(S, np.float64)
+    n = U.shape[1]
+    cv = lambda a: None if a is None else np.ascontiguousarray(a, np.float64)
+    dS, dU, dV = cv(dS), cv(dU), cv(dV)
+    dG = np.empty((4, n))
+    rc = lib().k2ref_gesvd2_bwd_d(n, _ptr(U), _ptr(S), _ptr(V), n, _ptr(dS), _ptr(dU), _ptr(dV), _ptr(dG), float(tau))
+    if rc != 0:
+        raise ValueError("k2ref_gesvd2_bwd_d returned %d" % rc)
+    return dG
+
+
+def kogbet(A, prec="d", max_sweeps=40, tol_factor=1.0):
+    """n x n Kogbetliantz SVD of one square matrix (column-major / any numpy array):
+    returns (U, S, V, sweeps, info) with A ~ U diag(S) V^T, S descending."""
+    T = _dt(prec)
+    A = np.asfortranarray(A, dtype=T)
+    n = A.shape[0]
+    U = np.empty((n, n), T, order="F"); V = np.empty((n, n), T, order="F"); S = np.empty(n, T)
+    sw = C.c_int32(0); info = C.c_int32(0)
+    rc = getattr(lib(), "k2ref_kogbet_" + prec)(n, _ptr(A), _ptr(U), _ptr(V), _ptr(S), int(max_sweeps),
+                                                 float(tol_factor), C.byref(sw), C.byref(info))
+    if rc != 0:
+        raise ValueError("k2ref_kogbet returned %d" % rc)
+    return U, S, V, sw.value, info.value
 
 
 def brute_sigma(g):

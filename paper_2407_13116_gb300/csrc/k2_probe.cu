@@ -1,0 +1,77 @@
+// Pipe-throughput probes (include/k2probe.h): the roofline denominators of the 2x2 SVD
+// kernels, measured on the device at hand.
+#include <cuda_runtime.h>
+
+#include "k2probe.h"
+
+namespace {
+
+constexpr int CHAINS = 8;
+
+template <typename T, int OP>
+__global__ void probe_kernel(T *out, int iters, T seed)
+{
+    T x[CHAINS];
+#pragma unroll
+    for (int i = 0; i < CHAINS; ++i) x[i] = seed + T(threadIdx.x) * T(1e-7) + T(i) * T(1e-3);
+    const T y = T(1.0000001), z = T(1e-9);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < CHAINS; ++i) {
+            if (OP == 0) x[i] = fma(x[i], y, z);
+            else if (OP == 1) x[i] = x[i] / (y + T(i));
+            else x[i] = sqrt(x[i] + z);
+        }
+    }
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < CHAINS; ++i) s += x[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T, int OP>
+int run(double *rate)
+{
+    int dev, sms;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1000;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1000;
+    const int threads = 256, blocks = sms * 8;
+    const int iters = (OP == 0) ? 4096 : 512;
+    T *buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(T) * (size_t)blocks * threads) != cudaSuccess) return -1000;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(a);
+        probe_kernel<T, OP><<<blocks, threads>>>(buf, iters, T(1));
+        cudaEventRecord(b);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(buf);
+    if (e != cudaSuccess) return -1000;
+    *rate = (double)blocks * threads * iters * CHAINS / (best * 1e-3);
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int k2probe_rate(int op, double *rate)
+{
+    switch (op) {
+    case 0: return run<double, 0>(rate);
+    case 1: return run<double, 1>(rate);
+    case 2: return run<double, 2>(rate);
+    case 3: return run<float, 0>(rate);
+    case 4: return run<float, 1>(rate);
+    case 5: return run<float, 2>(rate);
+    default: return -1;
+    }
+}

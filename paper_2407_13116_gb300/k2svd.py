@@ -44,10 +44,11 @@ def lib():
 
 
 def _bind_extra(L):
-    P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
-    if hasattr(L, "k2svd_dgesvd2_bwd"):
-        L.k2svd_dgesvd2_bwd.argtypes = [I64, P, P, P, I64, P, P, P, P, D, P]
-        L.k2svd_dgesvd2_bwd.restype = C.c_int
+    P, I64, I32, D, F = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_float
+    L.k2svd_dgesvd2_bwd.argtypes = [I64, P, P, P, I64, P, P, P, P, D, P]
+    L.k2svd_dgesvd2_bwd.restype = C.c_int
+    L.k2svd_sgesvd2_bwd.argtypes = [I64, P, P, P, I64, P, P, P, P, F, P]
+    L.k2svd_sgesvd2_bwd.restype = C.c_int
 
 
 def _ptr(t):
@@ -149,6 +150,32 @@ def trsvd2(F, Gu, H, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_e
     if rc != 0:
         raise K2SVDError("k2svd_%strsvd2 returned %d" % (p, rc))
     return U, V, S, Se, Sf, info
+
+
+def gesvd2_bwd(U, S, V, dS=None, dU=None, dV=None, gap_rtol=1e-10, dG=None):
+    """Adjoint of gesvd2: dG (4, n) from U, V (4, n), S (2, n) and the optional upstream
+    gradients dS (2, n), dU, dV (4, n).  All planes must share one leading dimension."""
+    p = _prefix(U.dtype)
+    dev = U.device
+    n = U.shape[1]
+    ld = _planes(U, 4, "U")
+    for t, nm, k in ((S, "S", 2), (V, "V", 4), (dS, "dS", 2), (dU, "dU", 4), (dV, "dV", 4)):
+        if t is None:
+            continue
+        _check(t, nm, U.dtype, dev)
+        if t.shape[1] != n or _planes(t, k, nm) != ld:
+            raise K2SVDError("%s must have shape (%d, %d) and the leading dimension of U" % (nm, k, n))
+    if dG is None:
+        dG = torch.empty((4, ld), dtype=U.dtype, device=dev)[:, :n]
+    _check(dG, "dG", U.dtype, dev)
+    if _planes(dG, 4, "dG") != ld:
+        raise K2SVDError("dG must have the leading dimension of U")
+    with torch.cuda.device(dev):
+        rc = getattr(lib(), "k2svd_%sgesvd2_bwd" % p)(n, _ptr(U), _ptr(S), _ptr(V), ld, _ptr(dS), _ptr(dU), _ptr(dV),
+                                                      _ptr(dG), float(gap_rtol), _stream())
+    if rc != 0:
+        raise K2SVDError("k2svd_%sgesvd2_bwd returned %d" % (p, rc))
+    return dG
 
 
 def to_planes(A):
