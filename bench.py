@@ -29,6 +29,7 @@ N_HALF_D = 1 << 27
 N_HALF_S = 1 << 28
 E2E_HALF = 1 << 25
 N_DIFF = 1 << 24
+N_KOG = 8192
 E2E_CHUNK = 1 << 22
 METRIC = "FP64 2×2 SVDs/s & % of roofline; fwd+bwd/s; batched Kogbetliantz speedup"
 BYTES_GE = {"d": 112, "s": 56}          # in 4 T + out (4 U + 4 V + 2 S) T
@@ -45,6 +46,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp32", action="store_true")
     p.add_argument("--no-fwd-bwd", action="store_true")
+    p.add_argument("--no-kog", action="store_true")
     p.add_argument("--profile-case", choices=["d", "s"], default=None,
                    help="run a small case of the 2x2 kernels (for ncu captures) and exit")
     p.add_argument("--profile-n", type=int, default=1 << 22)
@@ -301,6 +303,62 @@ def fwd_bwd_leg(steps, warmup, dev, D):
             "workload": "2^24 FP64 R(theta) diag(s1,s2) R(phi)^T, 10% near-equal singular values, upstream N(0,1)"}
 
 
+def kog_leg(steps, warmup, dev, D):
+    """Batched Kogbetliantz: 8192 FP64 matrices of order uniform in {8..128} (Q1 diag(sigma)
+    Q2^T, sigma log-uniform in [1e-12, 1]) to off-norm < n eps ||G||_F.  The persistent form
+    (one graph launch of per-bucket persistent kernels) is timed over `steps` runs; the
+    per-step form (three launches per step, a host read-back per sweep) once."""
+    import numpy as np
+    import torch
+    from paper_2407_13116_gb300 import inputs as I
+    from paper_2407_13116_gb300 import k2svd
+    orders = I.kog_orders(N_KOG, 8, 128, SEED + 4)
+    flat, _ = I.kog_batch(orders, SEED + 4)
+    A = torch.from_numpy(flat).to(dev)
+    n, offs, soffs, tot, stot = k2svd.kog_layout(orders)
+    U = torch.empty(tot, dtype=torch.float64, device=dev); V = torch.empty_like(U)
+    S = torch.empty(stot, dtype=torch.float64, device=dev)
+    sw = torch.empty(len(n), dtype=torch.int32, device=dev); info = torch.empty_like(sw)
+    ws = k2svd.kogbet_workspace(orders, torch.float64, k2svd.KOG_GRAPH, dev)
+    run = lambda fl, w: k2svd.kogbet(A, orders, flags=fl, workspace=w, U=U, V=V, S=S, sweeps=sw, info=info)
+    for _ in range(warmup + 1):                 # the first call tunes the block sizes
+        run(k2svd.KOG_GRAPH, ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    D.barrier()
+    e0.record()
+    for _ in range(steps):
+        run(k2svd.KOG_GRAPH, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    pers_ms = D.max(e0.elapsed_time(e1) / steps)
+    sweeps = sw.cpu().numpy().astype(np.int64)
+    conv = int((info.cpu().numpy() == 0).sum())
+    Sp = S.clone()
+    wsp = k2svd.kogbet_workspace(orders, torch.float64, k2svd.KOG_PLAIN, dev)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    run(k2svd.KOG_PLAIN, wsp)
+    torch.cuda.synchronize()
+    plain_ms = D.max((time.perf_counter() - t) * 1e3)
+    same = bool(torch.equal(Sp, S))
+    nn = orders.astype(np.int64)
+    # method's FP64 work: per sweep n(n-1)/2 pivots, each a 2x2 SVD (~239 FP64 slots, the
+    # general double count) and 16 FP64 operations per index (row, column, U and V rotations)
+    ops = float((sweeps * (nn * (nn - 1) // 2) * (16 * nn + 239)).sum())
+    peak = fp64_peak(2070.0)
+    del A, U, V, S, ws, wsp
+    torch.cuda.empty_cache()
+    return {"speedup_vs_per_step": plain_ms / pers_ms, "persistent_ms": pers_ms, "per_step_ms": plain_ms,
+            "matrices_per_gpu": N_KOG, "converged": conv, "mean_sweeps": float(sweeps.mean()),
+            "max_sweeps": int(sweeps.max()), "forms_bitwise_equal": same,
+            "roofline": {"bound": "alu", "achieved": ops / (pers_ms / 1e3) / 1e9, "peak": peak / 1e9,
+                         "unit": "G FP64-pipe op/s", "frac": ops / (pers_ms / 1e3) / peak,
+                         "ops": ops},
+            "workload": "8192 FP64 Q1 diag(sigma) Q2^T, n uniform in {8..128}, sigma log-uniform [1e-12,1], "
+                        "modulus strategy, off < n eps ||G||_F"}
+
+
 def e2e_leg(steps, warmup, dev):
     """End to end through the Python API: pinned host inputs -> device -> kernels -> host
     outputs, in chunks over two streams so that copies overlap the kernels."""
@@ -440,6 +498,8 @@ def run_ours(a):
                        "gesvd2_ms": rs["ge_ms"], "trsvd2_ms": rs["tr_ms"]}
     if not a.no_fwd_bwd:
         out["fwd_bwd"] = fwd_bwd_leg(a.steps, a.warmup, dev, D)
+    if not a.no_kog:
+        out["kogbet"] = kog_leg(max(2, a.steps // 3), 1, dev, D)
     if D.world == 1 and not a.no_e2e:
         out["e2e"] = e2e_leg(max(2, a.steps // 3), 1, dev)
     if D.rank == 0 and D.world == 1 and not a.no_cpu_baseline:

@@ -130,6 +130,80 @@ int k2svd_sgesvd2_bwd(int64_t batch, const float *U, const float *S, const float
                       float gap_rtol, void *stream);
 
 /*
+ * k2svd_dkogbet / k2svd_skogbet -- SVD of `batch` square matrices of uneven orders by the
+ * parallel Kogbetliantz method, eq. (SVD) of Sect. 1: G_{k+1} = U_k^T G_k V_k with
+ * U_{k+1} = U_k U_k-hat and V_{k+1} = V_k V_k-hat, where step k of a sweep transforms the
+ * disjoint pivot pairs of the parallel modulus strategy (all pairs i < j with
+ * i + j = k mod n, k = 0..n-1), each pivot [[g_ii, g_ij], [g_ji, g_jj]] decomposed by the
+ * 2x2 method of Sect. 3.  Order of a step: all pivot SVDs from G_k, all row rotations, all
+ * column rotations (U and V updated alike), then the pivot blocks set to diag(sigma1,
+ * sigma2).  A rotated pair (x, y) becomes (fma(m21, y, m11 x), fma(m22, y, m12 x)).  G is
+ * first scaled by the power of two that puts its largest element in [1/2, 1).  Sweeps stop
+ * when off(G) < tol_factor * n * eps * ||G||_F (eps = 2^-52 / 2^-23; the norms summed
+ * column by column in increasing index order) or after max_sweeps.  At exit a negative
+ * diagonal element is negated with its column of U; the singular values are sorted into
+ * descending order (stable), permuting U and V.  Results are bitwise
+ * reproducible and independent of the launch configuration.
+ *
+ *   batch        number of matrices, >= 0
+ *   n            HOST array of the orders, 1 <= n[i] <= 4096
+ *   offs         HOST array: matrix i's A, U and V start at element offs[i] of their
+ *                arrays, column-major with leading dimension n[i]
+ *   soffs        HOST array: matrix i's singular values start at element soffs[i] of S
+ *   A            input matrices (read only)
+ *   U, V         outputs (may not alias A), A_i = U_i diag(S_i) V_i^T
+ *   S            output singular values, descending, n[i] per matrix
+ *   sweeps, info nullable device arrays (one int32 per matrix): sweeps performed; info 0 =
+ *                converged, 1 = stopped at max_sweeps (the method never hangs)
+ *   max_sweeps   >= 0; tol_factor > 0 (1.0: the bound above); the per-step form needs
+ *                batch <= 65535
+ *   flags        K2SVD_KOG_PLAIN: one launch per step (the per-step form, for comparison);
+ *                K2SVD_KOG_GRAPH: capture the launches in a CUDA graph (cached for repeated
+ *                calls with the same arguments) and launch the graph;
+ *                K2SVD_KOG_NOTUNE: skip the block-size autotuner (defaults per order)
+ *   workspace    device scratch of ws_bytes bytes, 256-byte aligned, from k2svd_?kogbet_ws
+ *                for the same batch, n and flags; owned by the caller, not kept after the call
+ *                (a cached graph refers to it: keep it alive while reusing the same arguments)
+ * The persistent form groups the matrices by order into buckets; each bucket runs as one
+ * persistent launch (one CTA per matrix at a time, longest first, G in shared memory up to
+ * order 128 for double and 224 for float, else in the workspace), with the block size
+ * picked per bucket by timing (first call per device).  The host arrays are read during
+ * the call only.  Argument order for error codes: 1 batch, 2 n, 3 offs, 4 soffs, 5 A, 6 U,
+ * 7 V, 8 S, 11 max_sweeps, 12 tol_factor, 13 flags, 14 workspace, 15 ws_bytes.
+ */
+#define K2SVD_KOG_PLAIN  1
+#define K2SVD_KOG_GRAPH  2
+#define K2SVD_KOG_NOTUNE 4
+int k2svd_dkogbet_ws(int64_t batch, const int32_t *n, int32_t flags, size_t *ws_bytes);
+int k2svd_skogbet_ws(int64_t batch, const int32_t *n, int32_t flags, size_t *ws_bytes);
+int k2svd_dkogbet(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs,
+                  const double *A, double *U, double *V, double *S, int32_t *sweeps, int32_t *info,
+                  int32_t max_sweeps, double tol_factor, int32_t flags,
+                  void *workspace, size_t ws_bytes, void *stream);
+int k2svd_skogbet(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs,
+                  const float *A, float *U, float *V, float *S, int32_t *sweeps, int32_t *info,
+                  int32_t max_sweeps, double tol_factor, int32_t flags,
+                  void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * k2svd_dkog_sigma_bwd / k2svd_skog_sigma_bwd -- gradient of the singular values of the
+ * k2svd_?kogbet batch with respect to A: dA_i = U_i diag(dS_i) V_i^T (sigma = diag(U^T A V)
+ * with U, V held fixed; no paper counterpart).  Same n/offs/soffs description as
+ * k2svd_?kogbet; dS holds n[i] values per matrix at soffs[i]; dA is written like A.
+ * Element (r, c) is the sum over q = 0..n-1 in increasing order of (U_rq dS_q) V_cq with
+ * fma (bitwise reproducible).  batch <= 65535.  workspace: device scratch of at least
+ * 32 * batch bytes, 256-byte aligned (the k2svd_?kogbet workspace is large enough).
+ * Argument order for error codes: 1 batch, 2 n, 3 offs, 4 soffs, 5 U, 6 V, 7 dS, 8 dA,
+ * 9 workspace, 10 ws_bytes.
+ */
+int k2svd_dkog_sigma_bwd(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs,
+                         const double *U, const double *V, const double *dS, double *dA,
+                         void *workspace, size_t ws_bytes, void *stream);
+int k2svd_skog_sigma_bwd(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs,
+                         const float *U, const float *V, const float *dS, float *dA,
+                         void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * k2svd_version -- library version as major*10000 + minor*100 + patch.
  */
 int k2svd_version(void);

@@ -9,7 +9,7 @@ Functions whose result is not pinned by an independent check are marked
 "parity unpinned" in their docstrings.
 """
 from .k2ref import (build, lib, gesvd2, trsvd2, hypot, trace, efops, prec, effl, ext,
-                    brute_sigma, dmetrics, FLAGS, opcount, OPS, gesvd2_bwd, kogbet)
+                    brute_sigma, dmetrics, FLAGS, opcount, OPS, gesvd2_bwd, kogbet, kog_sigma_bwd)
 
 __all__ = ["build", "lib", "gesvd2", "trsvd2", "hypot", "trace", "efops", "prec", "effl",
-           "ext", "brute_sigma", "dmetrics", "FLAGS", "opcount", "OPS", "gesvd2_bwd", "kogbet"]
+           "ext", "brute_sigma", "dmetrics", "FLAGS", "opcount", "OPS", "gesvd2_bwd", "kogbet", "kog_sigma_bwd"]

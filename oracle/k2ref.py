@@ -93,6 +93,7 @@ def _bind_extra(L):
         fn = getattr(L, "k2ref_kogbet_" + sfx)
         fn.argtypes = [I32, P, P, P, P, C.c_int, D, P, P]
         fn.restype = C.c_int
+        getattr(L, "k2ref_kog_sigma_bwd_" + sfx).argtypes = [I32, P, P, P, P]
     if hasattr(L, "k2ref_gesvd2_bwd_d"):
         L.k2ref_gesvd2_bwd_d.argtypes = [I64, P, P, P, I64, P, P, P, P, D]
         L.k2ref_gesvd2_bwd_d.restype = C.c_int
@@ -220,6 +221,17 @@ def kogbet(A, prec="d", max_sweeps=40, tol_factor=1.0):
     if rc != 0:
         raise ValueError("k2ref_kogbet returned %d" % rc)
     return U, S, V, sw.value, info.value
+
+
+def kog_sigma_bwd(U, V, dS, prec="d"):
+    """dA = U diag(dS) V^T for one n x n matrix (column-major), in the order of the C ABI."""
+    T = _dt(prec)
+    U = np.asfortranarray(U, dtype=T); V = np.asfortranarray(V, dtype=T)
+    dS = np.ascontiguousarray(dS, dtype=T)
+    n = U.shape[0]
+    dA = np.empty((n, n), T, order="F")
+    getattr(lib(), "k2ref_kog_sigma_bwd_" + prec)(n, _ptr(U), _ptr(V), _ptr(dS), _ptr(dA))
+    return dA
 
 
 def brute_sigma(g):

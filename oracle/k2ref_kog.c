@@ -17,7 +17,10 @@
  *    fma-accumulated g_rc^2)), the column sums added in increasing c; the same order gives
  *    ||G||_F; the iteration stops when off(G) < tol_factor * n * eps * ||G||_F (eps = 2^-52
  *    or 2^-23) or after max_sweeps sweeps;
- *  - the diagonal is sorted into descending order (stable), permuting U and V.
+ *  - at exit a negative diagonal element g_ii (possible when the test holds before a
+ *    sweep has touched it) is negated together with column i of U (signs go to the left,
+ *    as in Sect. 3.1), then the diagonal is sorted into descending order (stable),
+ *    permuting U and V.
  */
 #include <math.h>
 #include <stdint.h>
@@ -55,6 +58,15 @@ int SFX(k2ref_kogbet)(int32_t n, const R *A, R *U, R *V, R *S, int max_sweeps, d
     R *pu = (R *)malloc(sizeof(R) * 4 * (size_t)n), *pv = (R *)malloc(sizeof(R) * 4 * (size_t)n);  \
     R *ps = (R *)malloc(sizeof(R) * 2 * (size_t)n);                                               \
     int *perm = (int *)malloc(sizeof(int) * (size_t)n);                                           \
+    int finite = 1;                                                                               \
+    for (size_t q = 0; q < nn; ++q) if (!isfinite(A[q])) finite = 0;                              \
+    if (!finite) {                 /* non-finite input: NaN outputs, info -1 */                   \
+        for (size_t q = 0; q < nn; ++q) { U[q] = NAN; V[q] = NAN; }                               \
+        for (int q = 0; q < n; ++q) S[q] = NAN;                                                   \
+        *sweeps = 0; *info = -1;                                                                  \
+        free(G); free(pi); free(pj); free(pu); free(pv); free(ps); free(perm);                    \
+        return 0;                                                                                 \
+    }                                                                                             \
     memcpy(G, A, nn * sizeof(R));                                                                 \
     for (size_t q = 0; q < nn; ++q) { U[q] = 0; V[q] = 0; }                                       \
     for (int q = 0; q < n; ++q) { U[(size_t)q * n + q] = 1; V[(size_t)q * n + q] = 1; }           \
@@ -101,6 +113,12 @@ int SFX(k2ref_kogbet)(int32_t n, const R *A, R *U, R *V, R *S, int max_sweeps, d
     }                                                                                             \
     *sweeps = sw;                                                                                 \
     *info = (off < tol || off == 0) ? 0 : 1;                                                      \
+    /* a negative diagonal element (left by an early exit) gives its sign to U's column */    \
+    for (int q = 0; q < n; ++q)                                                                   \
+        if (G[(size_t)q * n + q] < 0) {                                                           \
+            G[(size_t)q * n + q] = -G[(size_t)q * n + q];                                         \
+            for (int r = 0; r < n; ++r) U[(size_t)q * n + r] = -U[(size_t)q * n + r];             \
+        }                                                                                         \
     /* stable sort of the diagonal into descending order */                                      \
     for (int q = 0; q < n; ++q) perm[q] = q;                                                      \
     for (int a = 1; a < n; ++a) {                                                                 \
@@ -120,7 +138,22 @@ int SFX(k2ref_kogbet)(int32_t n, const R *A, R *U, R *V, R *S, int max_sweeps, d
     return 0;                                                                                     \
 }
 
+/* dA = U diag(dS) V^T: element (r, c) accumulates (U_rq dS_q) V_cq over q = 0..n-1 with fma. */
+#define SIGBWD_BODY(R, SFX, FMA)                                                                  \
+void SFX(k2ref_kog_sigma_bwd)(int32_t n, const R *U, const R *V, const R *dS, R *dA)             \
+{                                                                                                 \
+    for (int c = 0; c < n; ++c)                                                                   \
+        for (int r = 0; r < n; ++r) {                                                             \
+            R acc = 0;                                                                            \
+            for (int q = 0; q < n; ++q)                                                           \
+                acc = FMA(U[(size_t)q * n + r] * dS[q], V[(size_t)q * n + c], acc);               \
+            dA[(size_t)c * n + r] = acc;                                                          \
+        }                                                                                         \
+}
+
 #define SFXD(x) x##_d
 #define SFXS(x) x##_s
 KOG_BODY(double, SFXD, k2ref_pivot_d, fma, sqrt, scalbn, ilogb, 0x1p-52)
 KOG_BODY(float, SFXS, k2ref_pivot_s, fmaf, sqrtf, scalbnf, ilogbf, 0x1p-23f)
+SIGBWD_BODY(double, SFXD, fma)
+SIGBWD_BODY(float, SFXS, fmaf)

@@ -39,3 +39,33 @@ class SVD2x2(torch.autograd.Function):
 def svd2x2(A, gap_rtol=1e-10):
     """SVD of a batch of real 2x2 matrices with autograd support: returns (U, S, V)."""
     return SVD2x2.apply(A, gap_rtol)
+
+
+class KogbetSigma(torch.autograd.Function):
+    """Batched n x n SVD by the persistent Kogbetliantz driver with the gradient of the
+    singular values: dA_i = U_i diag(dS_i) V_i^T (k2svd_?kog_sigma_bwd).  Inputs and outputs
+    are packed (flat, column-major per matrix)."""
+
+    @staticmethod
+    def forward(ctx, A, orders, max_sweeps, flags):
+        U, S, V, sweeps, info = k2svd.kogbet(A, orders, max_sweeps=max_sweeps, flags=flags)
+        ctx.save_for_backward(U, V)
+        ctx.orders = list(orders)
+        ctx.mark_non_differentiable(U, V, sweeps, info)
+        ctx.set_materialize_grads(False)
+        return U, S, V, sweeps, info
+
+    @staticmethod
+    def backward(ctx, gU, gS, gV, gsw, ginfo):
+        if gU is not None or gV is not None:
+            raise k2svd.K2SVDError("kogbet_sigma differentiates the singular values only")
+        if gS is None:
+            return None, None, None, None
+        U, V = ctx.saved_tensors
+        dA = k2svd.kog_sigma_bwd(U, V, gS.contiguous(), ctx.orders)
+        return dA, None, None, None
+
+
+def kogbet_sigma(A, orders, max_sweeps=40, flags=0):
+    """(U, S, V, sweeps, info) of a packed batch, differentiable in S."""
+    return KogbetSigma.apply(A, list(orders), max_sweeps, flags)

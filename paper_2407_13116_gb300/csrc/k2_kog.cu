@@ -1,0 +1,784 @@
+// Batched n x n Kogbetliantz SVD (eq. (SVD) of Sect. 1) with the 2x2 method of Sect. 3 as
+// the pivot solver: k2svd_{d,s}kogbet, k2svd_{d,s}kogbet_ws, k2svd_{d,s}kog_sigma_bwd
+// (include/k2svd.h).
+//
+// Persistent form: the matrices are grouped by order into buckets.  Each bucket is one
+// persistent launch: every CTA takes the next matrix from a queue (largest first) and runs
+// all of its sweeps alone, with G in shared memory (orders up to 128 double / 224 float)
+// or in the workspace.  A step is three phases separated by block barriers: the pivot
+// SVDs (one thread per pivot), the row rotations (pair index fastest, so that a warp reads
+// consecutive rows), the column rotations with the U and V updates and the pivot blocks
+// (row index fastest).  The off-norm is summed column by column in a fixed order, so the
+// sweep count -- and every bit of the result -- does not depend on the launch shape.
+//
+// Per-step form (K2SVD_KOG_PLAIN): G in the workspace, three launches per step over the
+// whole batch, and a host read-back per sweep for the convergence test.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "k2_kog_dev.cuh"
+#include "k2svd.h"
+#include "k2_launch.h"
+
+namespace k2 {
+
+// ---------------------------------------------------------------------------------------
+// parameters and shared-memory layout
+// ---------------------------------------------------------------------------------------
+template <typename T> struct kog_params {
+    const kog_desc *desc;
+    int count;             // matrices in this launch
+    int *queue;            // work counter (persistent) / per-matrix flags (per-step)
+    const T *A;
+    T *U, *V, *S;
+    int32_t *sweeps, *info;
+    T *gws;                // G scratch base
+    int max_sweeps;
+    double tol_factor;
+    int nmax;              // largest order of the launch (shared-memory capacity)
+};
+
+template <typename T> __host__ __device__ constexpr size_t kog_piv_elems(int nmax) { return (size_t)(nmax / 2 + 1) * 10; }
+
+template <typename T>
+__host__ __device__ inline size_t kog_smem_bytes(int nmax, bool gg)
+{
+    size_t g = gg ? 0 : (size_t)(nmax + 1) * nmax * sizeof(T);
+    return g + kog_piv_elems<T>(nmax) * sizeof(T) + (size_t)nmax * sizeof(T) + 2 * (size_t)nmax * sizeof(int) + 64;
+}
+
+// ---------------------------------------------------------------------------------------
+// per-matrix phases shared by both forms (called by all threads of a block)
+// ---------------------------------------------------------------------------------------
+struct kog_sh {                       // block-shared scalars
+    int slot, kmax, bad;
+    double b;
+};
+
+// Load A into G (leading dimension ld), U = V = I; returns the prescaling exponent k, or
+// INT_MIN when A has a non-finite element (outputs set to NaN, info -1).
+template <typename T>
+__device__ int kog_load(const T *A, T *G, int ld, T *U, T *V, int n, kog_sh *sh)
+{
+    if (threadIdx.x == 0) { sh->kmax = INT_MIN; sh->bad = 0; }
+    __syncthreads();
+    int lmax = INT_MIN, bad = 0;
+    const int nn = n * n;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int r = e % n, c = e / n;
+        const T x = A[e];
+        if (!isfinite(x)) bad = 1;
+        else if (x != T(0)) lmax = max(lmax, fpt<T>::expo(x));
+        G[(size_t)c * ld + r] = x;
+        U[e] = (r == c) ? T(1) : T(0);
+        V[e] = (r == c) ? T(1) : T(0);
+    }
+    if (lmax != INT_MIN) atomicMax(&sh->kmax, lmax);
+    if (bad) atomicOr(&sh->bad, 1);
+    __syncthreads();
+    const int kmax = sh->kmax, isbad = sh->bad;
+    __syncthreads();
+    if (isbad) return INT_MIN;
+    const int k = (kmax == INT_MIN) ? 0 : -(kmax + 1);
+    if (k != 0)
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            T *g = &G[(size_t)(e / n) * ld + e % n];
+            *g = fpt<T>::scale(*g, k);
+        }
+    __syncthreads();
+    return k;
+}
+
+// One step (pivot SVDs, rows, columns + U + V + pivot blocks) on G with leading dimension ld.
+template <typename T>
+__device__ __forceinline__ void kog_step(T *G, int ld, T *U, T *V, int n, int st, T *piv)
+{
+    const int np = modulus_count(n, st);
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        int i, j;
+        modulus_pair(n, st, p, i, j);
+        kog_pivot(G[(size_t)i * ld + i], G[(size_t)i * ld + j], G[(size_t)j * ld + i], G[(size_t)j * ld + j], piv + 10 * p);
+    }
+    __syncthreads();
+    const int items = np * n;
+    for (int w = threadIdx.x; w < items; w += blockDim.x) {          // rows i, j <- U-hat^T
+        const int p = w % np, c = w / np;
+        int i, j;
+        modulus_pair(n, st, p, i, j);
+        rot2(G[(size_t)c * ld + i], G[(size_t)c * ld + j], piv + 10 * p);
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < items; w += blockDim.x) {          // columns i, j <- V-hat
+        const int r = w % n, p = w / n;
+        int i, j;
+        modulus_pair(n, st, p, i, j);
+        const T *m = piv + 10 * p;
+        if (r == i || r == j) {
+            G[(size_t)i * ld + r] = (r == i) ? m[8] : T(0);
+            G[(size_t)j * ld + r] = (r == j) ? m[9] : T(0);
+        } else {
+            rot2(G[(size_t)i * ld + r], G[(size_t)j * ld + r], m + 4);
+        }
+        rot2(U[(size_t)i * n + r], U[(size_t)j * n + r], m);
+        rot2(V[(size_t)i * n + r], V[(size_t)j * n + r], m + 4);
+    }
+    __syncthreads();
+}
+
+// Sort the diagonal (descending, stable), write S, permute the columns of U and V through
+// the staging area `stage` (n*n elements, may be G).
+template <typename T>
+__device__ void kog_finish(const T *G, int ld, T *U, T *V, T *S, int n, int k, T *dg, int *perm, T *stage)
+{
+    // a negative diagonal element gives its sign to U's column (stored in the sign of dg's
+    // slot as a flag array after the sort); |g_qq| are ranked
+    int *flip = perm + n;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const T d = G[(size_t)q * ld + q];
+        flip[q] = d < T(0);
+        dg[q] = d < T(0) ? -d : d;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const T dq = dg[q];
+        int rank = 0;
+        for (int p = 0; p < n; ++p) {
+            const T dp = dg[p];
+            rank += (dp > dq) || (dp == dq && p < q);
+        }
+        perm[rank] = q;
+        S[rank] = fpt<T>::scale(dq, -k);
+    }
+    __syncthreads();
+    const int nn = n * n;
+    for (int pass = 0; pass < 2; ++pass) {
+        T *X = pass ? V : U;
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) stage[e] = X[e];
+        __syncthreads();
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int src = perm[e / n];
+            const T x = stage[(size_t)src * n + e % n];
+            X[e] = (pass == 0 && flip[src]) ? -x : x;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ void kog_fail(T *U, T *V, T *S, int n)
+{
+    const T qn = T(NAN);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) { U[e] = qn; V[e] = qn; }
+    for (int q = threadIdx.x; q < n; q += blockDim.x) S[q] = qn;
+}
+
+// ---------------------------------------------------------------------------------------
+// persistent kernel
+// ---------------------------------------------------------------------------------------
+template <typename T, bool GG>
+__global__ void __launch_bounds__(512) kog_persistent(const kog_params<T> P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ kog_sh sh;
+    T *Gs = reinterpret_cast<T *>(smem);
+    T *piv = Gs + (GG ? 0 : (size_t)(P.nmax + 1) * P.nmax);
+    T *colsum = piv + kog_piv_elems<T>(P.nmax);
+    int *perm = reinterpret_cast<int *>(colsum + P.nmax);
+    for (;;) {
+        if (threadIdx.x == 0) sh.slot = atomicAdd(P.queue, 1);
+        __syncthreads();
+        const int slot = sh.slot;
+        __syncthreads();
+        if (slot >= P.count) break;
+        const kog_desc d = P.desc[slot];
+        const int n = d.n, ld = GG ? n : n + 1;
+        T *G = GG ? P.gws + d.goff : Gs;
+        T *U = P.U + d.off, *V = P.V + d.off, *S = P.S + d.soff;
+        const int k = kog_load(P.A + d.off, G, ld, U, V, n, &sh);
+        if (k == INT_MIN) {
+            kog_fail(U, V, S, n);
+            if (threadIdx.x == 0) {
+                if (P.sweeps) P.sweeps[d.idx] = 0;
+                if (P.info) P.info[d.idx] = -1;
+            }
+            __syncthreads();
+            continue;
+        }
+        T *bc = reinterpret_cast<T *>(&sh.b);
+        const T nrm = kog_norm(G, n, ld, false, colsum, bc);
+        const T tol = (T(P.tol_factor) * T(n)) * kog_eps<T>::v() * nrm;
+        T off = kog_norm(G, n, ld, true, colsum, bc);
+        int sw = 0;
+        while (!(off < tol) && sw < P.max_sweeps && off > T(0)) {
+            for (int st = 0; st < n; ++st) kog_step(G, ld, U, V, n, st, piv);
+            ++sw;
+            off = kog_norm(G, n, ld, true, colsum, bc);
+        }
+        kog_finish(G, ld, U, V, S, n, k, colsum, perm, G);
+        if (threadIdx.x == 0) {
+            if (P.sweeps) P.sweeps[d.idx] = sw;
+            if (P.info) P.info[d.idx] = (off < tol || off == T(0)) ? 0 : 1;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// per-step form: state per matrix in the workspace
+// ---------------------------------------------------------------------------------------
+template <typename T> struct kog_state {
+    T tol, off;
+    int k, sw, active, bad;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) kogp_init(const kog_params<T> P, kog_state<T> *state)
+{
+    __shared__ kog_sh sh;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *colsum = reinterpret_cast<T *>(smem);
+    const kog_desc d = P.desc[blockIdx.x];
+    const int n = d.n;
+    T *G = P.gws + d.goff, *U = P.U + d.off, *V = P.V + d.off;
+    const int k = kog_load(P.A + d.off, G, n, U, V, n, &sh);
+    kog_state<T> &s = state[blockIdx.x];
+    if (k == INT_MIN) {
+        kog_fail(U, V, P.S + d.soff, n);
+        if (threadIdx.x == 0) { s.bad = 1; s.active = 0; s.sw = 0; s.k = 0; }
+        return;
+    }
+    T *bc = reinterpret_cast<T *>(&sh.b);
+    const T nrm = kog_norm(G, n, n, false, colsum, bc);
+    const T tol = (T(P.tol_factor) * T(n)) * kog_eps<T>::v() * nrm;
+    const T off = kog_norm(G, n, n, true, colsum, bc);
+    if (threadIdx.x == 0) {
+        s.tol = tol; s.off = off; s.k = k; s.sw = 0; s.bad = 0;
+        s.active = (!(off < tol) && P.max_sweeps > 0 && off > T(0)) ? 1 : 0;
+        if (s.active) atomicAdd(P.queue, 1);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) kogp_pivots(const kog_params<T> P, const kog_state<T> *state, T *pivws,
+                                                   const int64_t *pivoff, int st)
+{
+    const int m = blockIdx.y;
+    if (!state[m].active) return;
+    const kog_desc d = P.desc[m];
+    if (st >= d.n) return;
+    const int np = modulus_count(d.n, st);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const T *G = P.gws + d.goff;
+    const int n = d.n;
+    int i, j;
+    modulus_pair(n, st, p, i, j);
+    kog_pivot(G[(size_t)i * n + i], G[(size_t)i * n + j], G[(size_t)j * n + i], G[(size_t)j * n + j],
+              pivws + pivoff[m] + 10 * p);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kogp_rows(const kog_params<T> P, const kog_state<T> *state, const T *pivws,
+                                                 const int64_t *pivoff, int st)
+{
+    const int m = blockIdx.y;
+    if (!state[m].active) return;
+    const kog_desc d = P.desc[m];
+    const int n = d.n;
+    if (st >= n) return;
+    const int np = modulus_count(n, st);
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= np * n) return;
+    const int p = w % np, c = w / np;
+    int i, j;
+    modulus_pair(n, st, p, i, j);
+    T *G = P.gws + d.goff;
+    rot2(G[(size_t)c * n + i], G[(size_t)c * n + j], pivws + pivoff[m] + 10 * p);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kogp_cols(const kog_params<T> P, const kog_state<T> *state, const T *pivws,
+                                                 const int64_t *pivoff, int st)
+{
+    const int m = blockIdx.y;
+    if (!state[m].active) return;
+    const kog_desc d = P.desc[m];
+    const int n = d.n;
+    if (st >= n) return;
+    const int np = modulus_count(n, st);
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= np * n) return;
+    const int r = w % n, p = w / n;
+    int i, j;
+    modulus_pair(n, st, p, i, j);
+    T *G = P.gws + d.goff, *U = P.U + d.off, *V = P.V + d.off;
+    const T *mm = pivws + pivoff[m] + 10 * p;
+    if (r == i || r == j) {
+        G[(size_t)i * n + r] = (r == i) ? mm[8] : T(0);
+        G[(size_t)j * n + r] = (r == j) ? mm[9] : T(0);
+    } else {
+        rot2(G[(size_t)i * n + r], G[(size_t)j * n + r], mm + 4);
+    }
+    rot2(U[(size_t)i * n + r], U[(size_t)j * n + r], mm);
+    rot2(V[(size_t)i * n + r], V[(size_t)j * n + r], mm + 4);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kogp_offnorm(const kog_params<T> P, kog_state<T> *state)
+{
+    __shared__ kog_sh sh;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *colsum = reinterpret_cast<T *>(smem);
+    kog_state<T> &s = state[blockIdx.x];
+    if (!s.active) return;
+    const kog_desc d = P.desc[blockIdx.x];
+    T *bc = reinterpret_cast<T *>(&sh.b);
+    const T off = kog_norm(P.gws + d.goff, d.n, d.n, true, colsum, bc);
+    if (threadIdx.x == 0) {
+        s.off = off;
+        s.sw += 1;
+        s.active = (!(off < s.tol) && s.sw < P.max_sweeps && off > T(0)) ? 1 : 0;
+        if (s.active) atomicAdd(P.queue, 1);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kogp_finish(const kog_params<T> P, const kog_state<T> *state)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const kog_state<T> s = state[blockIdx.x];
+    if (s.bad) {
+        if (threadIdx.x == 0) {
+            const kog_desc d = P.desc[blockIdx.x];
+            if (P.sweeps) P.sweeps[d.idx] = 0;
+            if (P.info) P.info[d.idx] = -1;
+        }
+        return;
+    }
+    const kog_desc d = P.desc[blockIdx.x];
+    const int n = d.n;
+    T *dg = reinterpret_cast<T *>(smem);
+    int *perm = reinterpret_cast<int *>(dg + P.nmax);
+    T *G = P.gws + d.goff;
+    kog_finish(G, n, P.U + d.off, P.V + d.off, P.S + d.soff, n, s.k, dg, perm, G);
+    if (threadIdx.x == 0) {
+        if (P.sweeps) P.sweeps[d.idx] = s.sw;
+        if (P.info) P.info[d.idx] = (s.off < s.tol || s.off == T(0)) ? 0 : 1;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// sigma gradient: dA = U diag(dS) V^T, one block per (column tile, matrix)
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) kog_sigma_bwd_kernel(const kog_desc *desc, const T *U, const T *V, const T *dS,
+                                                            T *dA)
+{
+    const kog_desc d = desc[blockIdx.y];
+    const int n = d.n;
+    const T *u = U + d.off, *v = V + d.off, *ds = dS + d.soff;
+    T *a = dA + d.off;
+    const int nn = n * n;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += gridDim.x * blockDim.x) {
+        const int r = e % n, c = e / n;
+        T acc = T(0);
+        for (int q = 0; q < n; ++q) acc = fma(u[(size_t)q * n + r] * ds[q], v[(size_t)q * n + c], acc);
+        a[e] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side: plan, workspace layout, autotuner, graph cache
+// ---------------------------------------------------------------------------------------
+template <typename T> struct kog_limits;
+template <> struct kog_limits<double> { static constexpr int SMEM_MAX_N = 128; };
+template <> struct kog_limits<float> { static constexpr int SMEM_MAX_N = 224; };
+
+static int bucket_of(int n, int smem_max)
+{
+    if (n <= 32) return 0;
+    if (n <= 64) return 1;
+    if (n <= 128) return 2;
+    if (n <= smem_max) return 3;
+    return 4;
+}
+static constexpr int NBUCKETS = 5;
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename T> struct kog_plan {
+    std::vector<kog_desc> desc;                      // sorted: bucket, then decreasing n
+    int bstart[NBUCKETS + 1];
+    int bnmax[NBUCKETS];
+    size_t off_desc, off_queue, off_g, off_state, off_piv, off_pivoff, total;
+    std::vector<int64_t> pivoff;                     // per-step form
+    bool plain;
+};
+
+template <typename T>
+static int make_plan(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs, int32_t flags,
+                     kog_plan<T> &pl)
+{
+    const int smax = kog_limits<T>::SMEM_MAX_N;
+    pl.plain = (flags & K2SVD_KOG_PLAIN) != 0;
+    pl.desc.resize((size_t)batch);
+    for (int64_t i = 0; i < batch; ++i) {
+        if (n[i] < 1 || n[i] > 4096) return -2;
+        kog_desc &d = pl.desc[(size_t)i];
+        d.n = n[i]; d.idx = (int32_t)i; d.off = offs ? offs[i] : 0; d.soff = soffs ? soffs[i] : 0; d.goff = 0;
+    }
+    std::stable_sort(pl.desc.begin(), pl.desc.end(), [&](const kog_desc &a, const kog_desc &b) {
+        int ba = bucket_of(a.n, smax), bb = bucket_of(b.n, smax);
+        if (ba != bb) return ba < bb;
+        return a.n > b.n;
+    });
+    for (int b = 0; b <= NBUCKETS; ++b) pl.bstart[b] = 0;
+    for (int b = 0; b < NBUCKETS; ++b) pl.bnmax[b] = 0;
+    for (size_t i = 0; i < pl.desc.size(); ++i) {
+        int b = bucket_of(pl.desc[i].n, smax);
+        pl.bstart[b + 1] = (int)i + 1;
+        pl.bnmax[b] = std::max(pl.bnmax[b], pl.desc[i].n);
+    }
+    for (int b = 1; b <= NBUCKETS; ++b) pl.bstart[b] = std::max(pl.bstart[b], pl.bstart[b - 1]);
+    // G scratch: every matrix in the per-step form, the global bucket in the persistent form
+    int64_t g = 0;
+    for (auto &d : pl.desc) {
+        if (pl.plain || bucket_of(d.n, smax) == 4) {
+            d.goff = g;
+            g += ((int64_t)d.n * d.n + 1) & ~(int64_t)1;
+        }
+    }
+    size_t off = 0;
+    pl.off_queue = off; off = align256(off + 128 * sizeof(int));
+    pl.off_desc = off; off = align256(off + pl.desc.size() * sizeof(kog_desc));
+    pl.off_g = off; off = align256(off + (size_t)g * sizeof(T));
+    pl.off_state = off;
+    pl.off_piv = off;
+    pl.off_pivoff = off;
+    if (pl.plain) {
+        off = align256(off + pl.desc.size() * sizeof(kog_state<T>));
+        pl.pivoff.resize(pl.desc.size());
+        int64_t pv = 0;
+        for (size_t i = 0; i < pl.desc.size(); ++i) { pl.pivoff[i] = pv; pv += (int64_t)(pl.desc[i].n / 2 + 1) * 10; }
+        pl.off_pivoff = off; off = align256(off + pl.desc.size() * sizeof(int64_t));
+        pl.off_piv = off; off = align256(off + (size_t)pv * sizeof(T));
+    }
+    pl.total = off;
+    return 0;
+}
+
+struct tune_key {
+    int dev, tsize, bucket;
+    bool operator<(const tune_key &o) const { return std::tie(dev, tsize, bucket) < std::tie(o.dev, o.tsize, o.bucket); }
+};
+static std::mutex g_mu;
+static std::map<tune_key, int> g_tuned;
+
+static int default_threads(int nmax) { return nmax <= 32 ? 128 : (nmax <= 64 ? 256 : 512); }
+
+template <typename T, bool GG>
+static cudaError_t launch_bucket(const kog_params<T> &P, int threads, cudaStream_t st, int *queue_dev)
+{
+    size_t smem = kog_smem_bytes<T>(P.nmax, GG);
+    cudaError_t e = cudaFuncSetAttribute(kog_persistent<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int blocks = 0;
+    if (grid_for(kog_persistent<T, GG>, threads, smem, &blocks) != 0) return cudaErrorUnknown;
+    if (blocks > P.count) blocks = P.count;
+    if (blocks < 1) return cudaSuccess;
+    e = cudaMemsetAsync(queue_dev, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    kog_persistent<T, GG><<<blocks, threads, smem, st>>>(P);
+    return cudaPeekAtLastError();
+}
+
+template <typename T>
+static cudaError_t launch_persistent(const kog_plan<T> &pl, kog_params<T> base, const int *threads, cudaStream_t st,
+                                     unsigned char *ws)
+{
+    const kog_desc *ddesc = reinterpret_cast<const kog_desc *>(ws + pl.off_desc);
+    int *queues = reinterpret_cast<int *>(ws + pl.off_queue);
+    for (int b = 0; b < NBUCKETS; ++b) {
+        int cnt = pl.bstart[b + 1] - pl.bstart[b];
+        if (cnt <= 0) continue;
+        kog_params<T> P = base;
+        P.desc = ddesc + pl.bstart[b];
+        P.count = cnt;
+        P.queue = queues + 16 * b;
+        P.nmax = pl.bnmax[b];
+        cudaError_t e = (b == 4) ? launch_bucket<T, true>(P, threads[b], st, P.queue)
+                                 : launch_bucket<T, false>(P, threads[b], st, P.queue);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Pick the block size of each bucket by timing a sample (the largest matrices of the
+// bucket, two per SM) on the caller's arrays; results are launch-shape independent.
+template <typename T>
+static int autotune(const kog_plan<T> &pl, const kog_params<T> &base, cudaStream_t st, unsigned char *ws, int dev,
+                    int *threads, bool tune)
+{
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int b = 0; b < NBUCKETS; ++b) {
+        int cnt = pl.bstart[b + 1] - pl.bstart[b];
+        threads[b] = default_threads(pl.bnmax[b]);
+        if (cnt <= 0) continue;
+        tune_key key{dev, (int)sizeof(T), b};
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) { threads[b] = it->second; continue; }
+        }
+        if (!tune) continue;
+        const int cand[3] = {128, 256, 512};
+        kog_params<T> P = base;
+        P.desc = reinterpret_cast<const kog_desc *>(ws + pl.off_desc) + pl.bstart[b];
+        P.count = std::min(cnt, 2 * sms);
+        P.queue = reinterpret_cast<int *>(ws + pl.off_queue) + 16 * b;
+        P.nmax = pl.bnmax[b];
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return K2SVD_ECUDA;
+        float best = 1e30f;
+        int bestt = threads[b];
+        for (int t : cand) {
+            if (t < 32) continue;
+            cudaEventRecord(e0, st);
+            cudaError_t e = (b == 4) ? launch_bucket<T, true>(P, t, st, P.queue) : launch_bucket<T, false>(P, t, st, P.queue);
+            cudaEventRecord(e1, st);
+            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0); cudaEventDestroy(e1);
+                return K2SVD_ECUDA;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; bestt = t; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        threads[b] = bestt;
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_tuned[key] = bestt;
+    }
+    return 0;
+}
+
+// Cache of instantiated graphs for repeated calls with the same arguments.
+struct graph_key {
+    std::vector<int64_t> sig;
+    bool operator<(const graph_key &o) const { return sig < o.sig; }
+};
+static std::map<graph_key, cudaGraphExec_t> g_graphs;
+
+template <typename T>
+static int kogbet_plain(const kog_plan<T> &pl, kog_params<T> base, cudaStream_t st, unsigned char *ws)
+{
+    const int m = (int)pl.desc.size();
+    kog_desc *ddesc = reinterpret_cast<kog_desc *>(ws + pl.off_desc);
+    kog_state<T> *state = reinterpret_cast<kog_state<T> *>(ws + pl.off_state);
+    T *pivws = reinterpret_cast<T *>(ws + pl.off_piv);
+    int64_t *pivoff = reinterpret_cast<int64_t *>(ws + pl.off_pivoff);
+    int *counter = reinterpret_cast<int *>(ws + pl.off_queue);
+    if (cudaMemcpyAsync(pivoff, pl.pivoff.data(), pl.pivoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return K2SVD_ECUDA;
+    int nmax = 0;
+    for (auto &d : pl.desc) nmax = std::max(nmax, d.n);
+    kog_params<T> P = base;
+    P.desc = ddesc; P.count = m; P.queue = counter; P.nmax = nmax;
+    const size_t sm_norm = (size_t)nmax * sizeof(T) + 2 * (size_t)nmax * sizeof(int) + 64;
+    if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return K2SVD_ECUDA;
+    kogp_init<T><<<m, 256, sm_norm, st>>>(P, state);
+    int remaining = 0;
+    if (cudaMemcpyAsync(&remaining, counter, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return K2SVD_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return K2SVD_ECUDA;
+    const int maxpairs = nmax / 2 + 1, maxitems = maxpairs * nmax;
+    for (int sw = 0; sw < base.max_sweeps && remaining > 0; ++sw) {
+        for (int s = 0; s < nmax; ++s) {
+            kogp_pivots<T><<<dim3((maxpairs + 127) / 128, m), 128, 0, st>>>(P, state, pivws, pivoff, s);
+            kogp_rows<T><<<dim3((maxitems + 255) / 256, m), 256, 0, st>>>(P, state, pivws, pivoff, s);
+            kogp_cols<T><<<dim3((maxitems + 255) / 256, m), 256, 0, st>>>(P, state, pivws, pivoff, s);
+        }
+        if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return K2SVD_ECUDA;
+        kogp_offnorm<T><<<m, 256, sm_norm, st>>>(P, state);
+        if (cudaMemcpyAsync(&remaining, counter, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return K2SVD_ECUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return K2SVD_ECUDA;
+    }
+    kogp_finish<T><<<m, 256, sm_norm, st>>>(P, state);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : K2SVD_ECUDA;
+}
+
+template <typename T>
+static int kogbet_ws(int64_t batch, const int32_t *n, int32_t flags, size_t *ws_bytes)
+{
+    if (batch < 0) return -1;
+    if (batch > 0 && !n) return -2;
+    if (!ws_bytes) return -4;
+    kog_plan<T> pl;
+    int rc = make_plan<T>(batch, n, nullptr, nullptr, flags, pl);
+    if (rc) return rc;
+    *ws_bytes = pl.total;
+    return 0;
+}
+
+template <typename T>
+static int kogbet(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs, const T *A, T *U, T *V,
+                  T *S, int32_t *sweeps, int32_t *info, int32_t max_sweeps, double tol_factor, int32_t flags,
+                  void *workspace, size_t ws_bytes, void *stream)
+{
+    if (batch < 0) return -1;
+    if (batch == 0) return 0;
+    if (!n) return -2;
+    if (!offs) return -3;
+    if (!soffs) return -4;
+    if (!A) return -5;
+    if (!U) return -6;
+    if (!V) return -7;
+    if (!S) return -8;
+    if (max_sweeps < 0) return -11;
+    if (!(tol_factor > 0)) return -12;
+    if (flags & ~(K2SVD_KOG_PLAIN | K2SVD_KOG_GRAPH | K2SVD_KOG_NOTUNE)) return -13;
+    if ((flags & K2SVD_KOG_PLAIN) && (flags & K2SVD_KOG_GRAPH)) return -13;
+    if (!workspace || ((uintptr_t)workspace & 255)) return -14;
+    kog_plan<T> pl;
+    int rc = make_plan<T>(batch, n, offs, soffs, flags, pl);
+    if (rc) return rc;
+    if (ws_bytes < pl.total) return -15;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    if (cudaMemcpyAsync(ws + pl.off_desc, pl.desc.data(), pl.desc.size() * sizeof(kog_desc), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return K2SVD_ECUDA;
+    kog_params<T> base;
+    base.desc = nullptr; base.count = 0; base.queue = nullptr;
+    base.A = A; base.U = U; base.V = V; base.S = S; base.sweeps = sweeps; base.info = info;
+    base.gws = reinterpret_cast<T *>(ws + pl.off_g);
+    base.max_sweeps = max_sweeps; base.tol_factor = tol_factor; base.nmax = 0;
+    if (pl.plain) {
+        if (batch > 65535) return -1;                  // one grid row per matrix
+        return kogbet_plain<T>(pl, base, st, ws);
+    }
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return K2SVD_ECUDA;
+    int threads[NBUCKETS];
+    const char *env = getenv("K2SVD_TUNE");
+    bool tune = !(flags & K2SVD_KOG_NOTUNE) && !(env && env[0] == '0');
+    if (autotune<T>(pl, base, st, ws, dev, threads, tune) != 0) return K2SVD_ECUDA;
+    if (!(flags & K2SVD_KOG_GRAPH))
+        return launch_persistent<T>(pl, base, threads, st, ws) == cudaSuccess ? 0 : K2SVD_ECUDA;
+    // graph: cached per (device, type, arguments, plan shape, block sizes)
+    graph_key key;
+    key.sig = {dev, (int64_t)sizeof(T), batch, (int64_t)(uintptr_t)A, (int64_t)(uintptr_t)U, (int64_t)(uintptr_t)V,
+               (int64_t)(uintptr_t)S, (int64_t)(uintptr_t)sweeps, (int64_t)(uintptr_t)info, max_sweeps,
+               (int64_t)(uintptr_t)workspace};
+    int64_t tbits;
+    std::memcpy(&tbits, &tol_factor, sizeof tbits);
+    key.sig.push_back(tbits);
+    for (int b = 0; b < NBUCKETS; ++b) { key.sig.push_back(threads[b]); key.sig.push_back(pl.bstart[b + 1]); key.sig.push_back(pl.bnmax[b]); }
+    for (auto &d : pl.desc) { key.sig.push_back(d.n); key.sig.push_back(d.off); key.sig.push_back(d.soff); }
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_graphs.find(key);
+        if (it != g_graphs.end()) exec = it->second;
+    }
+    if (!exec) {
+        cudaStream_t cap;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return K2SVD_ECUDA;
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { cudaStreamDestroy(cap); return K2SVD_ECUDA; }
+        cudaError_t e = launch_persistent<T>(pl, base, threads, cap, ws);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess || e2 != cudaSuccess) return K2SVD_ECUDA;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return K2SVD_ECUDA;
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_graphs.size() >= 16) {                 // bounded cache
+            cudaGraphExecDestroy(g_graphs.begin()->second);
+            g_graphs.erase(g_graphs.begin());
+        }
+        g_graphs[key] = exec;
+    }
+    return cudaGraphLaunch(exec, st) == cudaSuccess ? 0 : K2SVD_ECUDA;
+}
+
+template <typename T>
+static int kog_sigma_bwd(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs, const T *U,
+                         const T *V, const T *dS, T *dA, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (batch < 0 || batch > 65535) return -1;
+    if (batch == 0) return 0;
+    if (!n) return -2;
+    if (!offs) return -3;
+    if (!soffs) return -4;
+    if (!U) return -5;
+    if (!V) return -6;
+    if (!dS) return -7;
+    if (!dA) return -8;
+    if (!workspace || ((uintptr_t)workspace & 255)) return -9;
+    if (ws_bytes < (size_t)batch * sizeof(kog_desc)) return -10;
+    std::vector<kog_desc> desc((size_t)batch);
+    int nmax = 1;
+    for (int64_t i = 0; i < batch; ++i) {
+        if (n[i] < 1 || n[i] > 4096) return -2;
+        desc[(size_t)i] = kog_desc{n[i], (int32_t)i, offs[i], soffs[i], 0};
+        nmax = std::max(nmax, (int)n[i]);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    kog_desc *d_desc = static_cast<kog_desc *>(workspace);
+    if (cudaMemcpyAsync(d_desc, desc.data(), desc.size() * sizeof(kog_desc), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return K2SVD_ECUDA;
+    int xb = std::min(64, (nmax * nmax + 255) / 256);
+    kog_sigma_bwd_kernel<T><<<dim3(xb, (unsigned)batch), 256, 0, st>>>(d_desc, U, V, dS, dA);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : K2SVD_ECUDA;
+}
+
+}  // namespace k2
+
+extern "C" {
+
+int k2svd_dkogbet_ws(int64_t batch, const int32_t *n, int32_t flags, size_t *ws_bytes)
+{
+    return k2::kogbet_ws<double>(batch, n, flags, ws_bytes);
+}
+int k2svd_skogbet_ws(int64_t batch, const int32_t *n, int32_t flags, size_t *ws_bytes)
+{
+    return k2::kogbet_ws<float>(batch, n, flags, ws_bytes);
+}
+int k2svd_dkogbet(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs, const double *A, double *U,
+                  double *V, double *S, int32_t *sweeps, int32_t *info, int32_t max_sweeps, double tol_factor,
+                  int32_t flags, void *workspace, size_t ws_bytes, void *stream)
+{
+    return k2::kogbet<double>(batch, n, offs, soffs, A, U, V, S, sweeps, info, max_sweeps, tol_factor, flags, workspace,
+                              ws_bytes, stream);
+}
+int k2svd_skogbet(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs, const float *A, float *U,
+                  float *V, float *S, int32_t *sweeps, int32_t *info, int32_t max_sweeps, double tol_factor,
+                  int32_t flags, void *workspace, size_t ws_bytes, void *stream)
+{
+    return k2::kogbet<float>(batch, n, offs, soffs, A, U, V, S, sweeps, info, max_sweeps, tol_factor, flags, workspace,
+                             ws_bytes, stream);
+}
+int k2svd_dkog_sigma_bwd(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs, const double *U,
+                         const double *V, const double *dS, double *dA, void *workspace, size_t ws_bytes, void *stream)
+{
+    return k2::kog_sigma_bwd<double>(batch, n, offs, soffs, U, V, dS, dA, workspace, ws_bytes, stream);
+}
+int k2svd_skog_sigma_bwd(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs, const float *U,
+                         const float *V, const float *dS, float *dA, void *workspace, size_t ws_bytes, void *stream)
+{
+    return k2::kog_sigma_bwd<float>(batch, n, offs, soffs, U, V, dS, dA, workspace, ws_bytes, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// Device parts of the batched n x n Kogbetliantz SVD (eq. (SVD), Sect. 1): the parallel
+// modulus strategy, the rotations, the deterministic norms, and the per-matrix phases used
+// by both the persistent kernel and the per-step kernels.
+#pragma once
+#include <climits>
+#include <cstdint>
+
+#include "k2_svd2.cuh"
+
+namespace k2 {
+
+// One matrix of a batch.  G scratch (goff) is used when G does not live in shared memory.
+struct kog_desc {
+    int32_t n, idx;       // order, index in the caller's batch
+    int64_t off, soff;    // element offsets of A/U/V and of S
+    int64_t goff;         // element offset of this matrix's G in the workspace scratch
+};
+
+// Pair p of step k of the modulus strategy: the pairs i < j with i + j = k (mod n), in
+// increasing i: first i = 0 .. ceil(k/2)-1 with j = k - i, then i = k+1 .. with j = k + n - i.
+__device__ __forceinline__ int modulus_count(int n, int k) { return ((k + 1) >> 1) + ((n - k - 1) >> 1); }
+__device__ __forceinline__ void modulus_pair(int n, int k, int p, int &i, int &j)
+{
+    const int c1 = (k + 1) >> 1;
+    if (p < c1) { i = p; j = k - p; }
+    else { i = k + 1 + (p - c1); j = k + n - i; }
+}
+
+// (x, y) <- (fma(m21, y, m11 x), fma(m22, y, m12 x)), m column-major (m11, m21, m12, m22)
+template <typename T>
+__device__ __forceinline__ void rot2(T &x, T &y, const T *m)
+{
+    const T a = x, b = y;
+    x = fma(m[1], b, m[0] * a);
+    y = fma(m[3], b, m[2] * a);
+}
+
+template <typename T> struct kog_eps;
+template <> struct kog_eps<double> { __device__ static double v() { return 0x1p-52; } };
+template <> struct kog_eps<float> { __device__ static float v() { return 0x1p-23f; } };
+
+// Pivot SVD of [[a, b], [c, d]] (g11 = a, g21 = c, g12 = b, g22 = d) into m[10]:
+// U-hat (4, column-major, -0 as +0), V-hat (4), sigma1, sigma2 (rounded).
+template <typename T>
+__device__ __forceinline__ void kog_pivot(T g11, T g21, T g12, T g22, T *m)
+{
+    svd2_out<T> o;
+    svd2<T>(g11, g21, g12, g22, o);
+    m[0] = o.U.a11 + T(0); m[1] = o.U.a21 + T(0); m[2] = o.U.a12 + T(0); m[3] = o.U.a22 + T(0);
+    m[4] = o.V.a11 + T(0); m[5] = o.V.a21 + T(0); m[6] = o.V.a12 + T(0); m[7] = o.V.a22 + T(0);
+    m[8] = ef_fl(o.s1);
+    m[9] = ef_fl(o.s2);
+}
+
+// Block-level helpers.  All threads of the block (or the group running one matrix) call
+// them; `scratch` is shared memory for n values of T plus a few words.
+// sqrt of the column-sum-ordered sum of squares (diagonal skipped when off_only).
+template <typename T>
+__device__ __forceinline__ T kog_norm(const T *G, int n, int ld, bool off_only, T *colsum, T *bcast)
+{
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        T s = T(0);
+        const T *col = G + (size_t)c * ld;
+        for (int r = 0; r < n; ++r)
+            if (!off_only || r != c) s = fma(col[r], col[r], s);
+        colsum[c] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T tot = T(0);
+        for (int c = 0; c < n; ++c) tot = tot + colsum[c];
+        *bcast = sqrt(tot);
+    }
+    __syncthreads();
+    T r = *bcast;
+    __syncthreads();
+    return r;
+}
+
+}  // namespace k2

@@ -288,3 +288,28 @@ def kog_matrix(n, seed, index, smin=1e-12, dtype=np.float64):
     sigma = smin ** lu
     A = (qs[0] * sigma) @ qs[1].T
     return np.asfortranarray(A.astype(dtype)), np.sort(sigma)[::-1]
+
+
+def kog_batch(orders, seed, smin=1e-12, dtype=np.float64):
+    """Packed batch (flat, column-major per matrix) of Q1 diag(sigma) Q2^T for the given
+    orders, grouped by order: Q1, Q2 are the orthogonal factors of the Householder QR
+    (LAPACK) of N(0,1) matrices, i.e. products of n Householder reflectors built from
+    N(0,1) data; sigma log-uniform in [smin, 1].  Returns (flat, list of sigma arrays)."""
+    orders = np.asarray(orders, dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(orders ** 2)[:-1]]).astype(np.int64)
+    flat = np.empty(int((orders ** 2).sum()), dtype=dtype)
+    sigmas = [None] * len(orders)
+    for n in np.unique(orders):
+        idx = np.flatnonzero(orders == n)
+        b, n = len(idx), int(n)
+        z = normal((2, b, n, n), (seed * 7919 + n) & MASK64, 7)
+        q1 = np.linalg.qr(z[0])[0]
+        q2 = np.linalg.qr(z[1])[0]
+        u = uniform01(b * n, (seed * 7919 + n) & MASK64, 8).reshape(b, n)
+        sig = smin ** u
+        A = np.matmul(q1 * sig[:, None, :], np.swapaxes(q2, 1, 2))
+        At = np.ascontiguousarray(np.swapaxes(A, 1, 2)).reshape(b, n * n)   # column-major rows
+        for q, i in enumerate(idx):
+            flat[offs[i]:offs[i] + n * n] = At[q]
+            sigmas[i] = np.sort(sig[q])[::-1]
+    return flat.astype(dtype, copy=False), sigmas

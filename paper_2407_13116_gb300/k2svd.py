@@ -44,11 +44,21 @@ def lib():
 
 
 def _bind_extra(L):
-    P, I64, I32, D, F = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_float
+    P, I64, I32, D, F, SZ = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_float, C.c_size_t
     L.k2svd_dgesvd2_bwd.argtypes = [I64, P, P, P, I64, P, P, P, P, D, P]
     L.k2svd_dgesvd2_bwd.restype = C.c_int
     L.k2svd_sgesvd2_bwd.argtypes = [I64, P, P, P, I64, P, P, P, P, F, P]
     L.k2svd_sgesvd2_bwd.restype = C.c_int
+    for p in ("d", "s"):
+        f = getattr(L, "k2svd_%skogbet_ws" % p)
+        f.argtypes = [I64, P, I32, C.POINTER(SZ)]
+        f.restype = C.c_int
+        f = getattr(L, "k2svd_%skogbet" % p)
+        f.argtypes = [I64, P, P, P, P, P, P, P, P, P, I32, D, I32, P, SZ, P]
+        f.restype = C.c_int
+        f = getattr(L, "k2svd_%skog_sigma_bwd" % p)
+        f.argtypes = [I64, P, P, P, P, P, P, P, P, SZ, P]
+        f.restype = C.c_int
 
 
 def _ptr(t):
@@ -188,3 +198,93 @@ def from_planes(X, shape):
     """(4, n) planes -> (..., 2, 2)."""
     m = torch.stack([torch.stack([X[0], X[2]], -1), torch.stack([X[1], X[3]], -1)], -2)
     return m.reshape(*shape, 2, 2)
+
+
+# ------------------------------------------------------------------------------------------
+# batched n x n Kogbetliantz SVD
+# ------------------------------------------------------------------------------------------
+KOG_PLAIN, KOG_GRAPH, KOG_NOTUNE = 1, 2, 4
+
+
+def kog_layout(orders):
+    """Host arrays (n, offs, soffs) of a packed batch: matrix i occupies n_i^2 consecutive
+    elements (column-major), its singular values n_i consecutive elements."""
+    import numpy as np
+    n = np.ascontiguousarray(orders, dtype=np.int32)
+    sq = n.astype(np.int64) ** 2
+    offs = np.concatenate([[0], np.cumsum(sq)[:-1]]).astype(np.int64)
+    soffs = np.concatenate([[0], np.cumsum(n.astype(np.int64))[:-1]]).astype(np.int64)
+    return n, offs, soffs, int(sq.sum()), int(n.sum())
+
+
+def pack(mats):
+    """List of (n_i, n_i) tensors -> (flat column-major tensor, orders)."""
+    flat = torch.cat([m.t().contiguous().reshape(-1) for m in mats]) if mats else torch.empty(0)
+    return flat, [int(m.shape[0]) for m in mats]
+
+
+def unpack(flat, orders, square=True):
+    """Inverse of pack (square=True) or the split of a packed vector of singular values."""
+    out, o = [], 0
+    for n in orders:
+        k = n * n if square else n
+        x = flat[o:o + k]
+        out.append(x.reshape(n, n).t() if square else x)
+        o += k
+    return out
+
+
+def kogbet_workspace(orders, dtype, flags=0, device=None):
+    """A workspace tensor (uint8) sized by k2svd_?kogbet_ws for this batch and flags."""
+    n, _, _, _, _ = kog_layout(orders)
+    size = C.c_size_t(0)
+    rc = getattr(lib(), "k2svd_%skogbet_ws" % _prefix(dtype))(len(n), n.ctypes.data, int(flags), C.byref(size))
+    if rc != 0:
+        raise K2SVDError("k2svd_kogbet_ws returned %d" % rc)
+    return torch.empty((max(int(size.value), 256),), dtype=torch.uint8, device=device)
+
+
+def kogbet(A, orders, max_sweeps=40, tol_factor=1.0, flags=0, workspace=None, U=None, V=None, S=None,
+           sweeps=None, info=None):
+    """SVD of the packed batch A (flat, column-major per matrix, orders[i] each) by the
+    persistent Kogbetliantz driver (flags: KOG_PLAIN for the per-step form, KOG_GRAPH to
+    launch through a cached CUDA graph).  Returns (U, S, V, sweeps, info) packed like A."""
+    p = _prefix(A.dtype)
+    dev = A.device
+    n, offs, soffs, tot, stot = kog_layout(orders)
+    if A.dim() != 1 or A.numel() < tot or (A.numel() > 1 and A.stride(0) != 1):
+        raise K2SVDError("A must be a contiguous vector of at least %d elements" % tot)
+    U = torch.empty(tot, dtype=A.dtype, device=dev) if U is None else U
+    V = torch.empty(tot, dtype=A.dtype, device=dev) if V is None else V
+    S = torch.empty(stot, dtype=A.dtype, device=dev) if S is None else S
+    sweeps = torch.empty(len(n), dtype=torch.int32, device=dev) if sweeps is None else sweeps
+    info = torch.empty(len(n), dtype=torch.int32, device=dev) if info is None else info
+    for t, nm in ((U, "U"), (V, "V"), (S, "S")):
+        _check(t, nm, A.dtype, dev)
+    if workspace is None:
+        workspace = kogbet_workspace(orders, A.dtype, flags, dev)
+    with torch.cuda.device(dev):
+        rc = getattr(lib(), "k2svd_%skogbet" % p)(len(n), n.ctypes.data, offs.ctypes.data, soffs.ctypes.data,
+                                                  _ptr(A), _ptr(U), _ptr(V), _ptr(S), _ptr(sweeps), _ptr(info),
+                                                  int(max_sweeps), float(tol_factor), int(flags), _ptr(workspace),
+                                                  workspace.numel(), _stream())
+    if rc != 0:
+        raise K2SVDError("k2svd_%skogbet returned %d" % (p, rc))
+    return U, S, V, sweeps, info
+
+
+def kog_sigma_bwd(U, V, dS, orders, workspace=None, dA=None):
+    """dA = U diag(dS) V^T for every matrix of a packed batch."""
+    p = _prefix(U.dtype)
+    dev = U.device
+    n, offs, soffs, tot, stot = kog_layout(orders)
+    dA = torch.empty(tot, dtype=U.dtype, device=dev) if dA is None else dA
+    if workspace is None:
+        workspace = torch.empty((max(256, 32 * len(n)),), dtype=torch.uint8, device=dev)
+    with torch.cuda.device(dev):
+        rc = getattr(lib(), "k2svd_%skog_sigma_bwd" % p)(len(n), n.ctypes.data, offs.ctypes.data, soffs.ctypes.data,
+                                                         _ptr(U), _ptr(V), _ptr(dS), _ptr(dA), _ptr(workspace),
+                                                         workspace.numel(), _stream())
+    if rc != 0:
+        raise K2SVDError("k2svd_%skog_sigma_bwd returned %d" % (p, rc))
+    return dA
