@@ -1,0 +1,33 @@
+"""The C-ABI library builds (nvcc, sm_103a) and exports every function that include/*.h
+declares; no GPU is needed (nothing is called)."""
+import ctypes
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names.update(re.findall(r"^\s*int\s+(k2\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_headers_declare_the_abi():
+    names = _declared()
+    for must in ("k2svd_dgesvd2", "k2svd_sgesvd2", "k2svd_dtrsvd2", "k2svd_strsvd2", "k2svd_dgesvd2_bwd",
+                 "k2svd_dkogbet", "k2svd_skogbet", "k2svd_dkogbet_ws", "k2probe_rate"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2407_13116_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert lib.k2svd_version() == 100
