@@ -186,6 +186,34 @@ int k2svd_skogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
                   void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * k2svd_dkogbet_noalloc -- k2svd_dkogbet for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a service entry point.  Some callers may not
+ * allocate at all: a host whose device memory is entirely owned by another allocator (a
+ * framework's caching allocator that reserved it up front), a latency-critical path in
+ * which an allocation could block or fail, or a plugin that has no access to the
+ * allocator.  This entry needs no workspace: its scratch (the work queues, the descriptor
+ * table and, for orders above 128, the working copies of G) lives in one static device
+ * array of K2SVD_KOG_NOALLOC_BYTES bytes that every GPU holds from the time it loads the
+ * library until the process exits.  The call makes no device or host heap allocation.
+ *   Arguments, results and conventions are those of k2svd_dkogbet with the persistent
+ *   form and flags = 0, except that the block size is the one already tuned by an earlier
+ *   k2svd_dkogbet call on the device, or a default (results do not depend on it).
+ *   A problem whose scratch would exceed the array is rejected with K2SVD_ENOSPACE before
+ *   anything is launched; the scratch is 32 * batch bytes plus 8 * (n^2 + 1) bytes for
+ *   each order n above 128, each part rounded up to 256 bytes, plus 512 bytes (so up to
+ *   32752 matrices of orders <= 128).
+ *   The first call on a device looks up the address of that device's array with the device
+ *   current; make that first call before any stream capture.
+ *   All calls share the array and each call overwrites it: calls whose work overlaps on a
+ *   GPU (other streams, other host threads) race.  Serialize them, e.g. on one stream.
+ */
+#define K2SVD_ENOSPACE (-1001)
+#define K2SVD_KOG_NOALLOC_BYTES (1 << 20)
+int k2svd_dkogbet_noalloc(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs,
+                          const double *A, double *U, double *V, double *S, int32_t *sweeps, int32_t *info,
+                          int32_t max_sweeps, double tol_factor, void *stream);
+
+/*
  * k2svd_dkog_sigma_bwd / k2svd_skog_sigma_bwd -- gradient of the singular values of the
  * k2svd_?kogbet batch with respect to A: dA_i = U_i diag(dS_i) V_i^T (sigma = diag(U^T A V)
  * with U, V held fixed; no paper counterpart).  Same n/offs/soffs description as

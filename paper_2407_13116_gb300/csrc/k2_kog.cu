@@ -744,9 +744,115 @@ static int kog_sigma_bwd(int64_t batch, const int32_t *n, const int64_t *offs, c
     return cudaPeekAtLastError() == cudaSuccess ? 0 : K2SVD_ECUDA;
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free entry (k2svd_dkogbet_noalloc): the same persistent launches with the
+// scratch in a fixed array of every device that loads this library.
+// ---------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_kog_scratch[K2SVD_KOG_NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEV = 64;
+static std::mutex g_scratch_mu;
+static void *g_scratch_ptr[NOALLOC_MAX_DEV];
+// host staging of the descriptor table: static storage, so the call allocates nothing
+static kog_desc g_noalloc_desc[K2SVD_KOG_NOALLOC_BYTES / sizeof(kog_desc)];
+
+// Address of this device's scratch array, looked up once per device with it current.
+static int noalloc_scratch(void **p)
+{
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEV) return K2SVD_ECUDA;
+    if (!g_scratch_ptr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_kog_scratch) != cudaSuccess || !ptr) return K2SVD_ECUDA;
+        g_scratch_ptr[dev] = ptr;
+    }
+    *p = g_scratch_ptr[dev];
+    return 0;
+}
+
+static int kogbet_noalloc(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs, const double *A,
+                          double *U, double *V, double *S, int32_t *sweeps, int32_t *info, int32_t max_sweeps,
+                          double tol_factor, void *stream)
+{
+    if (batch < 0) return -1;
+    if (batch == 0) return 0;
+    if (!n) return -2;
+    if (!offs) return -3;
+    if (!soffs) return -4;
+    if (!A) return -5;
+    if (!U) return -6;
+    if (!V) return -7;
+    if (!S) return -8;
+    if (max_sweeps < 0) return -11;
+    if (!(tol_factor > 0)) return -12;
+    const int smax = kog_limits<double>::SMEM_MAX_N;
+    // scratch layout as the workspace of the persistent form: queues, descriptors, G of orders > 128
+    size_t bytes = align256(128 * sizeof(int)) + align256((size_t)batch * sizeof(kog_desc));
+    int64_t g = 0;
+    for (int64_t i = 0; i < batch; ++i) {
+        if (n[i] < 1 || n[i] > 4096) return -2;
+        if (bucket_of(n[i], smax) == 4) g += ((int64_t)n[i] * n[i] + 1) & ~(int64_t)1;
+    }
+    bytes += align256((size_t)g * sizeof(double));
+    if (bytes > (size_t)K2SVD_KOG_NOALLOC_BYTES) return K2SVD_ENOSPACE;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    void *scratch = nullptr;
+    if (noalloc_scratch(&scratch) != 0) return K2SVD_ECUDA;
+    kog_desc *desc = g_noalloc_desc;
+    for (int64_t i = 0; i < batch; ++i) desc[i] = kog_desc{n[i], (int32_t)i, offs[i], soffs[i], 0};
+    // bucket, then decreasing order, then index: the order of the persistent form's plan
+    std::sort(desc, desc + batch, [&](const kog_desc &a, const kog_desc &b) {
+        int ba = bucket_of(a.n, smax), bb = bucket_of(b.n, smax);
+        if (ba != bb) return ba < bb;
+        if (a.n != b.n) return a.n > b.n;
+        return a.idx < b.idx;
+    });
+    kog_plan<double> pl;                              // shape only; no containers are filled
+    for (int b = 0; b <= NBUCKETS; ++b) pl.bstart[b] = 0;
+    for (int b = 0; b < NBUCKETS; ++b) pl.bnmax[b] = 0;
+    int64_t goff = 0;
+    for (int64_t i = 0; i < batch; ++i) {
+        int b = bucket_of(desc[i].n, smax);
+        pl.bstart[b + 1] = (int)i + 1;
+        pl.bnmax[b] = std::max(pl.bnmax[b], desc[i].n);
+        if (b == 4) { desc[i].goff = goff; goff += ((int64_t)desc[i].n * desc[i].n + 1) & ~(int64_t)1; }
+    }
+    for (int b = 1; b <= NBUCKETS; ++b) pl.bstart[b] = std::max(pl.bstart[b], pl.bstart[b - 1]);
+    pl.off_queue = 0;
+    pl.off_desc = align256(128 * sizeof(int));
+    pl.off_g = pl.off_desc + align256((size_t)batch * sizeof(kog_desc));
+    pl.plain = false;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *ws = static_cast<unsigned char *>(scratch);
+    if (cudaMemcpyAsync(ws + pl.off_desc, desc, (size_t)batch * sizeof(kog_desc), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return K2SVD_ECUDA;
+    kog_params<double> base;
+    base.desc = nullptr; base.count = 0; base.queue = nullptr;
+    base.A = A; base.U = U; base.V = V; base.S = S; base.sweeps = sweeps; base.info = info;
+    base.gws = reinterpret_cast<double *>(ws + pl.off_g);
+    base.max_sweeps = max_sweeps; base.tol_factor = tol_factor; base.nmax = 0;
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return K2SVD_ECUDA;
+    int threads[NBUCKETS];
+    for (int b = 0; b < NBUCKETS; ++b) {             // tuned block sizes if known, else defaults
+        threads[b] = default_threads(pl.bnmax[b]);
+        std::lock_guard<std::mutex> lk2(g_mu);
+        auto it = g_tuned.find(tune_key{dev, (int)sizeof(double), b});
+        if (it != g_tuned.end()) threads[b] = it->second;
+    }
+    return launch_persistent<double>(pl, base, threads, st, ws) == cudaSuccess ? 0 : K2SVD_ECUDA;
+}
+
 }  // namespace k2
 
 extern "C" {
+
+int k2svd_dkogbet_noalloc(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs, const double *A,
+                          double *U, double *V, double *S, int32_t *sweeps, int32_t *info, int32_t max_sweeps,
+                          double tol_factor, void *stream)
+{
+    return k2::kogbet_noalloc(batch, n, offs, soffs, A, U, V, S, sweeps, info, max_sweeps, tol_factor, stream);
+}
 
 int k2svd_dkogbet_ws(int64_t batch, const int32_t *n, int32_t flags, size_t *ws_bytes)
 {
