@@ -33,6 +33,30 @@ __device__ __forceinline__ int clz128(u128 x)
 }
 
 // ---------------------------------------------------------------------------------------
+// IEEE comparisons done on the bit patterns (integer pipes), for operands that are never
+// NaN.  gt0/lt0 follow IEEE (+-0 is neither); pos_lt / pos_eq are for non-negative operands
+// (+0 .. +inf); eq0 is true for +0 and -0.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ bool lt0(double x) { int64_t b = (int64_t)dbits(x); return b < 0 && (b << 1) != 0; }
+__device__ __forceinline__ bool lt0(float x) { int32_t b = (int32_t)fbits(x); return b < 0 && (b << 1) != 0; }
+__device__ __forceinline__ bool eq0(double x) { return (dbits(x) << 1) == 0; }
+__device__ __forceinline__ bool eq0(float x) { return (fbits(x) << 1) == 0; }
+__device__ __forceinline__ bool pos_lt(double a, double b) { return dbits(a) < dbits(b); }
+__device__ __forceinline__ bool pos_lt(float a, float b) { return fbits(a) < fbits(b); }
+__device__ __forceinline__ bool pos_eq(double a, double b) { return dbits(a) == dbits(b); }
+__device__ __forceinline__ bool pos_eq(float a, float b) { return fbits(a) == fbits(b); }
+__device__ __forceinline__ bool is_inf(double x) { return (dbits(x) << 1) == (0x7FFull << 53); }
+__device__ __forceinline__ bool is_inf(float x) { return (fbits(x) << 1) == (0xFFu << 24); }
+__device__ __forceinline__ bool is_fin(double x) { return ((dbits(x) >> 52) & 0x7FF) != 0x7FF; }
+__device__ __forceinline__ bool is_fin(float x) { return ((fbits(x) >> 23) & 0xFF) != 0xFF; }
+// |a| < |b| for finite, non-NaN operands
+__device__ __forceinline__ bool abs_lt(double a, double b) { return (dbits(a) << 1) < (dbits(b) << 1); }
+__device__ __forceinline__ bool abs_lt(float a, float b) { return (fbits(a) << 1) < (fbits(b) << 1); }
+// -0 -> +0, anything else unchanged
+__device__ __forceinline__ double unneg0(double x) { uint64_t b = dbits(x); return dfrom(b == D_SIGN ? 0 : b); }
+__device__ __forceinline__ float unneg0(float x) { uint32_t b = fbits(x); return ffrom(b == F_SIGN ? 0u : b); }
+
+// ---------------------------------------------------------------------------------------
 // Per-type traits: exponent/mantissa split, exact scaling, constants.
 // For x != 0 finite: e = floor(lg|x|) (also for subnormals) and f = x 2^-e, 1 <= |f| < 2.
 // ---------------------------------------------------------------------------------------
@@ -128,52 +152,62 @@ template <typename T> struct ef { int e; T f; };
 template <typename T> __device__ __forceinline__ ef<T> ef_of(T x)
 {
     ef<T> w;
-    if (x == T(0)) { w.e = 0; w.f = T(0); }
+    if (eq0(x)) { w.e = 0; w.f = T(0); }
     else fpt<T>::split(x, w.e, w.f);
     return w;
 }
 template <typename T> __device__ __forceinline__ T ef_fl(ef<T> w) { return fpt<T>::ldexp_rn(w.f, w.e); }
 
 // eq. (binary): x (.) y; the mantissa product lies in [1,4)
+// Renormalise a product in [1,4) or a quotient in (1/2,2) (or 0) to (e, f), 1 <= |f| < 2, by
+// moving the binary exponent of z (exact, integer pipes).
+__device__ __forceinline__ void renorm(double z, int e, int &eo, double &fo)
+{
+    uint64_t b = dbits(z);
+    int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0) { eo = 0; fo = 0.0; return; }          // only z = 0 occurs here
+    eo = e + (E - 1023);
+    fo = dfrom((b & ~(0x7FFull << 52)) | (1023ull << 52));
+}
+__device__ __forceinline__ void renorm(float z, int e, int &eo, float &fo)
+{
+    uint32_t b = fbits(z);
+    int E = (int)((b >> 23) & 0xFF);
+    if (E == 0) { eo = 0; fo = 0.0f; return; }
+    eo = e + (E - 127);
+    fo = ffrom((b & ~(0xFFu << 23)) | (127u << 23));
+}
 template <typename T> __device__ __forceinline__ ef<T> ef_mul(ef<T> x, ef<T> y)
 {
-    T z = x.f * y.f;
     ef<T> w;
-    if (z == T(0)) { w.e = 0; w.f = T(0); return w; }
-    w.e = x.e + y.e;
-    if (fabs(z) >= T(2)) { z = z * T(0.5); w.e += 1; }
-    w.f = z;
+    renorm(x.f * y.f, x.e + y.e, w.e, w.f);
     return w;
 }
 // eq. (binary): x (/) y; the mantissa quotient lies in (1/2, 2)
 template <typename T> __device__ __forceinline__ ef<T> ef_div(ef<T> x, ef<T> y)
 {
-    T z = x.f / y.f;
     ef<T> w;
-    if (z == T(0)) { w.e = 0; w.f = T(0); return w; }
-    w.e = x.e - y.e;
-    if (fabs(z) < T(1)) { z = z * T(2); w.e -= 1; }
-    w.f = z;
+    renorm(x.f / y.f, x.e - y.e, w.e, w.f);
     return w;
 }
 // eq. (unary): 2^c (.) x
 template <typename T> __device__ __forceinline__ ef<T> ef_pow2(int c, ef<T> x)
 {
-    if (x.f != T(0)) x.e += c;
+    if (!eq0(x.f)) x.e += c;
     return x;
 }
-// eq. (prec)
+// eq. (prec) for the non-negative values that occur here (sign(f) is 0 or 1)
 template <typename T> __device__ __forceinline__ bool ef_prec(ef<T> x, ef<T> y)
 {
-    int sx = (x.f > T(0)) - (x.f < T(0)), sy = (y.f > T(0)) - (y.f < T(0));
+    int sx = eq0(x.f) ? 0 : 1, sy = eq0(y.f) ? 0 : 1;
     if (sx != sy) return sx < sy;
-    return (x.e < y.e) || ((x.e == y.e) && (x.f < y.f));
+    return (x.e < y.e) || ((x.e == y.e) && pos_lt(x.f, y.f));
 }
 // eq. (plus), x, y > 0 finite
 template <typename T> __device__ __forceinline__ ef<T> ef_plus(T x, T y)
 {
     T z = x + y;
-    if (z <= fpt<T>::nu()) return ef_of(z);
+    if (is_fin(z)) return ef_of(z);
     z = x * T(0.5) + y * T(0.5);
     ef<T> w = ef_of(z);
     w.e += 1;
@@ -183,9 +217,9 @@ template <typename T> __device__ __forceinline__ ef<T> ef_plus(T x, T y)
 template <typename T> __device__ __forceinline__ ef<T> ef_minus(T x, T y)
 {
     ef<T> w;
-    if (x == y) { w.e = 0; w.f = T(0); return w; }
+    if (pos_eq(x, y)) { w.e = 0; w.f = T(0); return w; }
     T z = x - y;
-    if (fabs(z) >= fpt<T>::mu()) return ef_of(z);
+    if (!abs_lt(z, fpt<T>::mu())) return ef_of(z);
     int ex = fpt<T>::expo(x), ey = fpt<T>::expo(y);
     int c = fpt<T>::EMU + fpt<T>::P - 1 - (ex < ey ? ex : ey);
     z = fpt<T>::scale(x, c) - fpt<T>::scale(y, c);

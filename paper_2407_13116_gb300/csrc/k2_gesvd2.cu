@@ -24,7 +24,7 @@ template <typename T> struct svd_args {
     int64_t n;
 };
 
-template <typename T> __device__ __forceinline__ T pz(T x) { return x + T(0); }   // -0 -> +0
+template <typename T> __device__ __forceinline__ T pz(T x) { return unneg0(x); }   // -0 -> +0
 
 template <typename T, bool TRI>
 __global__ void __launch_bounds__(128) svd2_kernel(const svd_args<T> a)
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(128) svd2_kernel(const svd_args<T> a)
         const T g12 = a.g2[i];
         const T g22 = a.g3[i];
         svd2_out<T> o;
-        if (isfinite(g11) && isfinite(g21) && isfinite(g12) && isfinite(g22)) {
+        if (is_fin(g11) && is_fin(g21) && is_fin(g12) && is_fin(g22)) {
             svd2<T>(g11, g21, g12, g22, o);
         } else {
             const T qn = T(NAN);

@@ -46,8 +46,8 @@ __device__ __forceinline__ void kog_pivot(T g11, T g21, T g12, T g22, T *m)
 {
     svd2_out<T> o;
     svd2<T>(g11, g21, g12, g22, o);
-    m[0] = o.U.a11 + T(0); m[1] = o.U.a21 + T(0); m[2] = o.U.a12 + T(0); m[3] = o.U.a22 + T(0);
-    m[4] = o.V.a11 + T(0); m[5] = o.V.a21 + T(0); m[6] = o.V.a12 + T(0); m[7] = o.V.a22 + T(0);
+    m[0] = unneg0(o.U.a11); m[1] = unneg0(o.U.a21); m[2] = unneg0(o.U.a12); m[3] = unneg0(o.U.a22);
+    m[4] = unneg0(o.V.a11); m[5] = unneg0(o.V.a21); m[6] = unneg0(o.V.a12); m[7] = unneg0(o.V.a22);
     m[8] = ef_fl(o.s1);
     m[9] = ef_fl(o.s2);
 }

@@ -51,17 +51,20 @@ template <typename T> __device__ __forceinline__ void swap_cols(m22<T> &m)
     T t = m.a11; m.a11 = m.a12; m.a12 = t;
     t = m.a21; m.a21 = m.a22; m.a22 = t;
 }
+// IEEE negation (a sign-bit flip) on the integer pipes
+__device__ __forceinline__ double ngt(double x) { return dfrom(dbits(x) ^ D_SIGN); }
+__device__ __forceinline__ float ngt(float x) { return ffrom(fbits(x) ^ F_SIGN); }
 template <typename T> __device__ __forceinline__ void neg_row(m22<T> &m, int r)
 {
-    if (r == 0) { m.a11 = -m.a11; m.a12 = -m.a12; } else { m.a21 = -m.a21; m.a22 = -m.a22; }
+    if (r == 0) { m.a11 = ngt(m.a11); m.a12 = ngt(m.a12); } else { m.a21 = ngt(m.a21); m.a22 = ngt(m.a22); }
 }
 template <typename T> __device__ __forceinline__ void neg_col(m22<T> &m, int c)
 {
-    if (c == 0) { m.a11 = -m.a11; m.a21 = -m.a21; } else { m.a12 = -m.a12; m.a22 = -m.a22; }
+    if (c == 0) { m.a11 = ngt(m.a11); m.a21 = ngt(m.a21); } else { m.a12 = ngt(m.a12); m.a22 = ngt(m.a22); }
 }
 template <typename T> __device__ __forceinline__ m22<T> rot(T c, T s)     // [[c,-s],[s,c]]
 {
-    m22<T> m; m.a11 = c; m.a21 = s; m.a12 = -s; m.a22 = c; return m;
+    m22<T> m; m.a11 = c; m.a21 = s; m.a12 = ngt(s); m.a22 = c; return m;
 }
 template <typename T> __device__ __forceinline__ m22<T> ident()
 {
@@ -94,17 +97,17 @@ __device__ __forceinline__ void simple9(int tt, T g11, T g21, T g12, T g22, m22<
     case 4: pv = true; a = g12; break;
     case 8: pu = true; pv = true; a = g22; break;
     case 9:
-        if (fabs(g11) < fabs(g22)) { pu = pv = true; a = g22; b = g11; } else { a = g11; b = g22; }
+        if (abs_lt(g11, g22)) { pu = pv = true; a = g22; b = g11; } else { a = g11; b = g22; }
         break;
     case 6:
-        if (fabs(g12) < fabs(g21)) { pu = true; a = g21; b = g12; } else { pv = true; a = g12; b = g21; }
+        if (abs_lt(g12, g21)) { pu = true; a = g21; b = g12; } else { pv = true; a = g12; b = g21; }
         break;
     default: break;
     }
     U = ident<T>();
     if (pu) swap_rows(U);
-    if (a < T(0)) neg_col(U, 0);
-    if (b < T(0)) neg_col(U, 1);
+    if (lt0(a)) neg_col(U, 0);
+    if (lt0(b)) neg_col(U, 1);
     V = ident<T>();
     if (pv) swap_rows(V);
     d1 = fabs(a); d2 = fabs(b);
@@ -119,9 +122,9 @@ __device__ __forceinline__ void simple35(int tt, T g11, T g21, T g12, T g22, m22
     T x0, x1;
     if (col) { p0 = (tt == 12); x0 = p0 ? g12 : g11; x1 = p0 ? g22 : g21; }
     else { p0 = (tt == 10); x0 = p0 ? g21 : g11; x1 = p0 ? g22 : g12; }
-    bool n0 = x0 < T(0), n1 = x1 < T(0);
+    bool n0 = lt0(x0), n1 = lt0(x1);
     T y0 = fabs(x0), y1 = fabs(x1);
-    bool p1 = y0 < y1;
+    bool p1 = pos_lt(y0, y1);
     T x = p1 ? y1 : y0, y = p1 ? y0 : y1;
     T c, s;
     cos_sin(y / x, c, s);
@@ -146,30 +149,30 @@ template <typename T> struct tri_out {
 template <typename T>
 __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int &flags)
 {
-    z.swap = r11 < r22;
+    z.swap = pos_lt(r11, r22);
     T ra = z.swap ? r22 : r11, rb = r12, rc = z.swap ? r11 : r22;
     if (z.swap) flags |= FL_SWAP;
     ef<T> era = ef_of(ra), erb = ef_of(rb), erc = ef_of(rc);
     T t2;
     bool t2inf = false;
-    if (ra == rc) {                                        // eq. (t2f'')
+    if (pos_eq(ra, rc)) {                                        // eq. (t2f'')
         t2 = (T(2) * rc) / rb;
         flags |= FL_T2F2;
-    } else if (rb == rc) {                                 // eq. (t2f''')
+    } else if (pos_eq(rb, rc)) {                                 // eq. (t2f''')
         t2 = ef_fl(ef_div(ef_mul(ef_pow2(1, erb), erc), ef_mul(era, era)));
         flags |= FL_T2F3;
-    } else if (ra / rb < fpt<T>::eps()) {                 // eq. (t2f''), only for t' ~ 13
+    } else if (pos_lt(ra / rb, fpt<T>::eps())) {                 // eq. (t2f''), only for t' ~ 13
         t2 = (T(2) * rc) / rb;
         flags |= FL_T2F2;
     } else {                                               // eq. (t2f')
         T h = hypot_cr(ra, rb);
-        if (h == rc) { t2 = T(0); t2inf = true; }
+        if (pos_eq(h, rc)) { t2 = T(0); t2inf = true; }
         else {
             ef<T> s = ef_plus(h, rc), d = ef_minus(h, rc);
             t2 = ef_fl(ef_div(ef_mul(ef_pow2(1, erb), erc), ef_mul(d, s)));
         }
     }
-    if (isinf(t2)) t2inf = true;
+    if (is_inf(t2)) t2inf = true;
     T tf;
     if (t2inf) { tf = T(1); flags |= FL_T2INF; }
     else tf = t2 / (T(1) + hypot_cr(t2, T(1)));           // eq. (tf)
@@ -181,7 +184,7 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
     T t = fma(rc, tf, rb);                                 // eq. (tp)
     T tp = t / ra;
     ef<T> s1, s2;
-    if (isinf(tp)) {                                       // eqs. (tp'), (s'')
+    if (is_inf(tp)) {                                       // eqs. (tp'), (s'')
         ef<T> et = ef_of(t);
         ef<T> ecos = ef_div(era, et);
         z.cpsi = ef_fl(ecos);
@@ -207,7 +210,7 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
 template <typename T> __device__ __forceinline__ m22<T> ucheck(const tri_out<T> &z)
 {
     m22<T> m;
-    if (z.swap) { m.a11 = z.spsi; m.a21 = z.cpsi; m.a12 = z.cpsi; m.a22 = -z.spsi; }
+    if (z.swap) { m.a11 = z.spsi; m.a21 = z.cpsi; m.a12 = z.cpsi; m.a22 = ngt(z.spsi); }
     else m = rot(z.cphi, z.sphi);
     if (z.psig) swap_cols(m);
     return m;
@@ -215,7 +218,7 @@ template <typename T> __device__ __forceinline__ m22<T> ucheck(const tri_out<T> 
 template <typename T> __device__ __forceinline__ m22<T> vcheck(const tri_out<T> &z)
 {
     m22<T> m;
-    if (z.swap) { m.a11 = z.sphi; m.a21 = z.cphi; m.a12 = z.cphi; m.a22 = -z.sphi; }
+    if (z.swap) { m.a11 = z.sphi; m.a21 = z.cphi; m.a12 = z.cphi; m.a22 = ngt(z.sphi); }
     else m = rot(z.cpsi, z.spsi);
     if (z.psig) swap_cols(m);
     return m;
@@ -224,20 +227,20 @@ template <typename T> __device__ __forceinline__ m22<T> vcheck(const tri_out<T> 
 template <typename T>
 __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
 {
-    const int t = (g11 != T(0)) | ((g21 != T(0)) << 1) | ((g12 != T(0)) << 2) | ((g22 != T(0)) << 3);
+    const int t = !eq0(g11) | (!eq0(g21) << 1) | (!eq0(g12) << 2) | (!eq0(g22) << 3);
     const int cls = cls_of(t);
     int s = 0, flags = 0;
     if (cls != 9) {                                        // eqs. (eG), (s): class 9 is not scaled
         int eG = INT_MIN;
-        if (g11 != T(0)) eG = max(eG, fpt<T>::expo(g11));
-        if (g21 != T(0)) eG = max(eG, fpt<T>::expo(g21));
-        if (g12 != T(0)) eG = max(eG, fpt<T>::expo(g12));
-        if (g22 != T(0)) eG = max(eG, fpt<T>::expo(g22));
+        if (!eq0(g11)) eG = max(eG, fpt<T>::expo(g11));
+        if (!eq0(g21)) eG = max(eG, fpt<T>::expo(g21));
+        if (!eq0(g12)) eG = max(eG, fpt<T>::expo(g12));
+        if (!eq0(g22)) eG = max(eG, fpt<T>::expo(g22));
         s = fpt<T>::ENU - eG - (cls == 15 ? 2 : 1);
         g11 = fpt<T>::scale(g11, s); g21 = fpt<T>::scale(g21, s);
         g12 = fpt<T>::scale(g12, s); g22 = fpt<T>::scale(g22, s);
     }
-    const int tp = (g11 != T(0)) | ((g21 != T(0)) << 1) | ((g12 != T(0)) << 2) | ((g22 != T(0)) << 3);
+    const int tp = !eq0(g11) | (!eq0(g21) << 1) | (!eq0(g12) << 2) | (!eq0(g22) << 3);
     const int clsp = cls_of(tp);
     bool simple = true;
     T d1 = T(0), d2 = T(0);
@@ -255,9 +258,9 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
         else if (tp == 11) { a = g22; b = g21; d = g11; }
         else if (tp == 14) { a = g21; b = g22; d = g12; }
         else { a = g11; b = g12; d = g22; }
-        bool n11 = a < T(0); a = fabs(a); if (n11) b = -b;
-        bool n12 = b < T(0); b = fabs(b); if (n12) d = -d;
-        bool n22 = d < T(0); d = fabs(d);
+        bool n11 = lt0(a); a = fabs(a); if (n11) b = ngt(b);
+        bool n12 = lt0(b); b = fabs(b); if (n12) d = ngt(d);
+        bool n22 = lt0(d); d = fabs(d);
         tri_out<T> z;
         tri_svd(a, b, d, z, flags);
         m22<T> U = ucheck(z);                              // U = P_U S11 S22 U-check
@@ -271,48 +274,48 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
     } else {
         // Sect. 3.2.2: fully pivoted URV of a matrix without zeros
         T w1 = hypot_cr(g11, g21), w2 = hypot_cr(g12, g22);
-        bool pv = w1 < w2;
+        bool pv = pos_lt(w1, w2);
         if (pv) { T x = g11; g11 = g12; g12 = x; x = g21; g21 = g22; g22 = x; w1 = w2; }
-        bool n1a = g11 < T(0), n1b = g21 < T(0);            // S1
-        if (n1a) { g11 = -g11; g12 = -g12; }
-        if (n1b) { g21 = -g21; g22 = -g22; }
-        bool pu = g11 < g21;
+        bool n1a = lt0(g11), n1b = lt0(g21);            // S1
+        if (n1a) { g11 = ngt(g11); g12 = ngt(g12); }
+        if (n1b) { g21 = ngt(g21); g22 = ngt(g22); }
+        bool pu = pos_lt(g11, g21);
         if (pu) { T x = g11; g11 = g21; g21 = x; x = g12; g12 = g22; g22 = x; }
         // eq. (QR15)
         const T tth = g21 / g11;
         const T secth = hypot_cr(tth, T(1));
         T r11 = w1, r12, r22;
-        if (fma(tth, g11, -g21) == T(0)) {                // tan(theta) exact: Lemma 3.4
+        if (eq0(fma(tth, g11, ngt(g21)))) {                // tan(theta) exact: Lemma 3.4
             r12 = fma(g22, tth, g12) / secth;
-            r22 = fma(-g12, tth, g22) / secth;
-        } else if ((g12 < T(0)) == (g22 < T(0))) {         // Thm. 3.5: r22 by eq. (EXT)
+            r22 = fma(ngt(g12), tth, g22) / secth;
+        } else if (lt0(g12) == lt0(g22)) {         // Thm. 3.5: r22 by eq. (EXT)
             r12 = fma(g22, tth, g12) / secth;
             r22 = ext_num_div(g22, g11, g12, g21, true, g11) / secth;
             flags |= FL_EXT;
         } else {                                           // Thm. 3.5: r12 by eq. (EXT)
-            r22 = fma(-g12, tth, g22) / secth;
+            r22 = fma(ngt(g12), tth, g22) / secth;
             r12 = ext_num_div(g12, g11, g22, g21, false, g11) / secth;
             flags |= FL_EXT;
         }
-        if (r12 == T(0) || r22 == T(0)) {
+        if (eq0(r12) || eq0(r22)) {
             // R'' of type 9 (or 1) or 5: finish as Sect. 3.1, G' = S1 P_U U_theta R'' P_V^T
             flags |= FL_FALLBACK;
             const T cth = T(1) / secth, sth = tth / secth;
             m22<T> Ur, Vr;
-            if (r12 == T(0)) {
-                simple9<T>(r22 != T(0) ? 9 : 1, r11, T(0), T(0), r22, Ur, Vr, d1, d2);
+            if (eq0(r12)) {
+                simple9<T>(!eq0(r22) ? 9 : 1, r11, T(0), T(0), r22, Ur, Vr, d1, d2);
             } else {
                 simple35<T>(5, r11, T(0), r12, T(0), Ur, Vr, d1);
                 d2 = T(0);
             }
             // U_theta Ur, with Ur a signed permutation: pick and negate columns of U_theta
             m22<T> M;
-            bool c0first = Ur.a11 != T(0);                 // non-zero of column 0 in row 0
+            bool c0first = !eq0(Ur.a11);                 // non-zero of column 0 in row 0
             T sg0 = c0first ? Ur.a11 : Ur.a21, sg1 = c0first ? Ur.a22 : Ur.a12;
-            T u0a = c0first ? cth : -sth, u0b = c0first ? sth : cth;   // U_theta column k0
-            T u1a = c0first ? -sth : cth, u1b = c0first ? cth : sth;   // U_theta column k1
-            M.a11 = sg0 < T(0) ? -u0a : u0a; M.a21 = sg0 < T(0) ? -u0b : u0b;
-            M.a12 = sg1 < T(0) ? -u1a : u1a; M.a22 = sg1 < T(0) ? -u1b : u1b;
+            T u0a = c0first ? cth : ngt(sth), u0b = c0first ? sth : cth;   // U_theta column k0
+            T u1a = c0first ? ngt(sth) : cth, u1b = c0first ? cth : sth;   // U_theta column k1
+            M.a11 = lt0(sg0) ? ngt(u0a) : u0a; M.a21 = lt0(sg0) ? ngt(u0b) : u0b;
+            M.a12 = lt0(sg1) ? ngt(u1a) : u1a; M.a22 = lt0(sg1) ? ngt(u1b) : u1b;
             if (pu) swap_rows(M);
             if (n1a) neg_row(M, 0);
             if (n1b) neg_row(M, 1);
@@ -321,10 +324,10 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
             o.V = Vr;
         } else {
             simple = false;
-            bool n12 = r12 < T(0);
-            if (n12) { r12 = -r12; r22 = -r22; }            // R'' S12
-            bool n22 = r22 < T(0);
-            if (n22) r22 = -r22;                           // S22 R'
+            bool n12 = lt0(r12);
+            if (n12) { r12 = ngt(r12); r22 = ngt(r22); }            // R'' S12
+            bool n22 = lt0(r22);
+            if (n22) r22 = ngt(r22);                           // S22 R'
             tri_out<T> z;
             tri_svd(r11, r12, r22, z, flags);
             m22<T> V = vcheck(z);                          // V = P_V S12 V-check
@@ -335,20 +338,20 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
             const bool plus = !n22;
             const T tb = z.swap ? T(1) / z.tanpsi : z.tanphi;
             T ca, sa;
-            if (isinf(tb)) {
+            if (is_inf(tb)) {
                 const T cth = T(1) / secth, sth = tth / secth;
-                ca = plus ? -sth : sth; sa = cth;
+                ca = plus ? ngt(sth) : sth; sa = cth;
             } else {
                 const T N = plus ? tb + tth : tb - tth;
-                const T D = plus ? fma(-tb, tth, T(1)) : fma(tb, tth, T(1));
-                if (D == T(0)) { ca = T(0); sa = N < T(0) ? T(-1) : T(1); }
+                const T D = plus ? fma(ngt(tb), tth, T(1)) : fma(tb, tth, T(1));
+                if (eq0(D)) { ca = T(0); sa = lt0(N) ? T(-1) : T(1); }
                 else {
                     const T ta = N / D;
-                    if (isinf(ta)) { ca = T(0); sa = N < T(0) ? T(-1) : T(1); }
+                    if (is_inf(ta)) { ca = T(0); sa = lt0(N) ? T(-1) : T(1); }
                     else {
                         T c0, s0;
                         cos_sin(ta, c0, s0);
-                        if (D < T(0)) { ca = -c0; sa = -s0; } else { ca = c0; sa = s0; }
+                        if (lt0(D)) { ca = ngt(c0); sa = ngt(s0); } else { ca = c0; sa = s0; }
                     }
                 }
             }
