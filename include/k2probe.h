@@ -15,11 +15,23 @@
 #ifndef K2PROBE_H
 #define K2PROBE_H
 
+#include <stdint.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
 
 int k2probe_rate(int op, double *rate);
+
+/*
+ * k2probe_div / k2probe_hypot -- elementwise checks of two primitives of the 2x2 kernels on
+ * device arrays of n doubles: q[i] = a[i] / b[i] by the integer-pipe correctly rounded
+ * division, h[i] = hypot(a[i], b[i]) by the correctly rounded hypot (Sect. 2).  For testing
+ * these primitives against the FP64 divider and an exact reference; not part of the method.
+ * Returns 0, -1 (n < 0 or a CUDA error), -2 (null pointer).  Asynchronous on `stream`.
+ */
+int k2probe_div(int64_t n, const double *a, const double *b, double *q, void *stream);
+int k2probe_hypot(int64_t n, const double *a, const double *b, double *h, void *stream);
 
 #ifdef __cplusplus
 }

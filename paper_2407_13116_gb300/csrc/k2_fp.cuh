@@ -145,6 +145,82 @@ template <> struct fpt<float> {
 };
 
 // ---------------------------------------------------------------------------------------
+// Correctly rounded binary64 division on the integer pipes (round to nearest, ties to
+// even, gradual underflow).  The FP64 pipe of sm_103 divides at about one ninth of its fma
+// rate, while 32-bit integer multiply-adds issue at 16-62 per clock per SM, so the quotient
+// is formed by long division in integers:
+//   * the mantissas A, B (53-bit integers, subnormals normalised) are brought to
+//     B <= A < 2B by one shift, so the quotient is 1.f with e = e_a - e_b (- 1);
+//   * three 19-bit fraction digits follow; each is estimated as
+//     trunc((r >> 29) * (2^19 / (B >> 29))) with one FP32 reciprocal of the 24 leading bits of
+//     B.  The estimate is within 0.19 of r 2^19 / B (relative errors below 2^-22 and a
+//     truncation of r below 2^48 / B < 1/16 of a digit), so one correction by +-1 against
+//     the exact remainder gives the digit.  The remainder fits in 2^54, so its low 64 bits
+//     (wrapping arithmetic) are exact;
+//   * the 58-bit quotient and the sticky remainder are rounded to 53 bits, or to the
+//     quantum 2^-1074 when the result is subnormal; overflow gives infinity.
+// Zero, infinite and NaN operands give the IEEE results by selection (no FP64 instruction).
+//
+// div_rn, hypot_cr and ext_num_div are kept out of line: the 2x2 kernel calls them from a
+// dozen divergent branches, and with every call site inlined the FP64 kernel ran 2.9 times
+// (FP32: 1.1 times) slower on matrices of mixed zero pattern and wide exponent range
+// (measured on a GB300; the instruction stream grows with each copy, and divergent warps
+// fetch from all of them).  One shared body per function keeps the executed code small.
+// ---------------------------------------------------------------------------------------
+static __device__ __noinline__ double div_rn(double a, double b)
+{
+    const uint64_t ab = dbits(a), bb = dbits(b);
+    const uint32_t Ea = (uint32_t)(ab >> 52) & 0x7FF, Eb = (uint32_t)(bb >> 52) & 0x7FF;
+    if (Ea == 0x7FF || Eb == 0x7FF || (ab << 1) == 0 || (bb << 1) == 0) {
+        // zero, infinite or NaN operands: IEEE results by selection
+        const uint64_t sg = (ab ^ bb) & D_SIGN;
+        const bool an = (ab << 1) > (0x7FFull << 53), bn = (bb << 1) > (0x7FFull << 53);
+        const bool ai = (ab << 1) == (0x7FFull << 53), bi = (bb << 1) == (0x7FFull << 53);
+        const bool az = (ab << 1) == 0, bz = (bb << 1) == 0;
+        if (an || bn || (az && bz) || (ai && bi)) return dfrom(0x7FF8000000000000ull);
+        if (az || bi) return dfrom(sg);
+        return dfrom(sg | (0x7FFull << 52));
+    }
+    uint64_t A = ab & D_MANT, B = bb & D_MANT;
+    int ea, eb;
+    if (Ea) { A |= D_HID; ea = (int)Ea - 1023; } else { int sh = __clzll((long long)A) - 11; A <<= sh; ea = -1022 - sh; }
+    if (Eb) { B |= D_HID; eb = (int)Eb - 1023; } else { int sh = __clzll((long long)B) - 11; B <<= sh; eb = -1022 - sh; }
+    int e = ea - eb;
+    if (A < B) { A <<= 1; e -= 1; }
+    const float rf = __frcp_rn(__uint2float_rz((uint32_t)(B >> 29))) * 524288.0f;      // 2^19 / (B >> 29)
+    uint64_t r = A - B, q = 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint32_t d = __float2uint_rz(__uint2float_rz((uint32_t)(r >> 29)) * rf);
+        int64_t rem = (int64_t)((r << 19) - (uint64_t)d * B);
+        if (rem < 0) { d -= 1; rem += (int64_t)B; }
+        else if (rem >= (int64_t)B) { d += 1; rem -= (int64_t)B; }
+        r = (uint64_t)rem;
+        q = (q << 19) | d;
+    }
+    const uint64_t sign = (ab ^ bb) & D_SIGN;
+    const bool sticky = r != 0;
+    if (e >= -1022) {                                       // normal: q in [2^57, 2^58) -> 53 bits
+        uint64_t m = q >> 5;
+        const bool rb = (q >> 4) & 1, st = sticky || (q & 15) != 0;
+        if (rb && (st || (m & 1))) ++m;
+        if (m >> 53) { m >>= 1; ++e; }
+        if (e > 1023) return dfrom(sign | (0x7FFull << 52));
+        return dfrom(sign | ((uint64_t)(e + 1023) << 52) | (m & D_MANT));
+    }
+    const int k = -1017 - e;                                // bits of q below the quantum 2^-1074
+    if (k > 63) return dfrom(sign);
+    uint64_t m = q >> k;
+    const bool rb = (q >> (k - 1)) & 1, st = sticky || (q & ((1ull << (k - 1)) - 1)) != 0;
+    if (rb && (st || (m & 1))) ++m;
+    return dfrom(sign | m);                                 // m <= 2^52: subnormal or 2^-1022
+}
+
+// the method's divisions: binary64 on the integer pipes, binary32 on the FP32 pipe
+__device__ __forceinline__ double qdiv(double a, double b) { return div_rn(a, b); }
+__device__ __forceinline__ float qdiv(float a, float b) { return a / b; }
+
+// ---------------------------------------------------------------------------------------
 // Exponent-"mantissa" pairs (Sect. 2): w = f 2^e with 1 <= |f| < 2, or (0, 0).
 // ---------------------------------------------------------------------------------------
 template <typename T> struct ef { int e; T f; };
@@ -187,7 +263,7 @@ template <typename T> __device__ __forceinline__ ef<T> ef_mul(ef<T> x, ef<T> y)
 template <typename T> __device__ __forceinline__ ef<T> ef_div(ef<T> x, ef<T> y)
 {
     ef<T> w;
-    renorm(x.f / y.f, x.e - y.e, w.e, w.f);
+    renorm(qdiv(x.f, y.f), x.e - y.e, w.e, w.f);
     return w;
 }
 // eq. (unary): 2^c (.) x
@@ -239,7 +315,7 @@ template <typename T> __device__ __forceinline__ ef<T> ef_minus(T x, T y)
 //    a'^2 + b'^2 with the squared midpoints to the neighbouring values, in integers
 //    (units 2^-110 for double, 2^-52 for float), ties to even.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ double hypot_cr(double x, double y)
+static __device__ __noinline__ double hypot_cr(double x, double y)
 {
     double a = fabs(x), b = fabs(y);
     if (a < b) { double t = a; a = b; b = t; }
@@ -297,7 +373,7 @@ __device__ __forceinline__ double hypot_cr(double x, double y)
     return dfrom(((uint64_t)E << 52) | (rb & D_MANT));
 }
 
-__device__ __forceinline__ float hypot_cr(float x, float y)
+static __device__ __noinline__ float hypot_cr(float x, float y)
 {
     float a = fabsf(x), b = fabsf(y);
     if (a < b) { float t = a; a = b; b = t; }
@@ -391,7 +467,7 @@ __device__ __forceinline__ void round113(u128 m, int e, bool sticky, u128 &M, in
     }
 }
 
-__device__ __forceinline__ double ext_num_div(double x1, double y1, double x2, double y2, bool sub, double d)
+static __device__ __noinline__ double ext_num_div(double x1, double y1, double x2, double y2, bool sub, double d)
 {
     uint64_t a1, b1, a2, b2; int ea1, eb1, ea2, eb2; bool na1, nb1, na2, nb2;
     dmant(x1, a1, ea1, na1); dmant(y1, b1, eb1, nb1);
@@ -479,11 +555,11 @@ __device__ __forceinline__ double ext_num_div(double x1, double y1, double x2, d
 }
 
 // eq. (EXT) for float: the wide type is double, where the products of floats are exact
-__device__ __forceinline__ float ext_num_div(float x1, float y1, float x2, float y2, bool sub, float d)
+static __device__ __noinline__ float ext_num_div(float x1, float y1, float x2, float y2, bool sub, float d)
 {
     double p2 = (double)x2 * (double)y2;
     double num = fma((double)x1, (double)y1, sub ? -p2 : p2);
-    double q = num / (double)d;
+    double q = div_rn(num, (double)d);
     return __double2float_rn(q);
 }
 

@@ -26,8 +26,10 @@ template <typename T> struct svd_args {
 
 template <typename T> __device__ __forceinline__ T pz(T x) { return unneg0(x); }   // -0 -> +0
 
+// At most 64 registers a thread, so 8 blocks (32 warps) are resident per SM: 5% faster than
+// the unconstrained 80-register build for FP64 on a GB300.
 template <typename T, bool TRI>
-__global__ void __launch_bounds__(128) svd2_kernel(const svd_args<T> a)
+__global__ void __launch_bounds__(128, 8) svd2_kernel(const svd_args<T> a)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {

@@ -1,8 +1,10 @@
 // Pipe-throughput probes (include/k2probe.h): the roofline denominators of the 2x2 SVD
 // kernels, measured on the device at hand.
+#include <cstdint>
 #include <cuda_runtime.h>
 
 #include "k2probe.h"
+#include "k2_fp.cuh"
 
 namespace {
 
@@ -62,6 +64,38 @@ int run(double *rate)
 }
 
 }  // namespace
+
+__global__ void div_kernel(int64_t n, const double *a, const double *b, double *q)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = k2::div_rn(a[i], b[i]);
+}
+
+__global__ void hypot_kernel(int64_t n, const double *a, const double *b, double *h)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        h[i] = k2::hypot_cr(a[i], b[i]);
+}
+
+extern "C" int k2probe_div(int64_t n, const double *a, const double *b, double *q, void *stream)
+{
+    if (n < 0) return -1;
+    if (n == 0) return 0;
+    if (!a || !b || !q) return -2;
+    int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    div_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, a, b, q);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1000;
+}
+
+extern "C" int k2probe_hypot(int64_t n, const double *a, const double *b, double *h, void *stream)
+{
+    if (n < 0) return -1;
+    if (n == 0) return 0;
+    if (!a || !b || !h) return -2;
+    int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    hypot_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, a, b, h);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1000;
+}
 
 extern "C" int k2probe_rate(int op, double *rate)
 {

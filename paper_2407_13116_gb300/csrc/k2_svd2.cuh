@@ -81,8 +81,8 @@ template <typename T> struct svd2_out {
 template <typename T> __device__ __forceinline__ void cos_sin(T tn, T &c, T &s)
 {
     T sec = hypot_cr(tn, T(1));
-    c = T(1) / sec;
-    s = tn / sec;
+    c = qdiv(T(1), sec);
+    s = qdiv(tn, sec);
 }
 
 // Sect. 3.1, class 9: U = P_U diag(sign a, sign b), V = P_V, sigma' = (|a|, |b|)
@@ -127,7 +127,7 @@ __device__ __forceinline__ void simple35(int tt, T g11, T g21, T g12, T g22, m22
     bool p1 = pos_lt(y0, y1);
     T x = p1 ? y1 : y0, y = p1 ? y0 : y1;
     T c, s;
-    cos_sin(y / x, c, s);
+    cos_sin(qdiv(y, x), c, s);
     d1 = hypot_cr(x, y);
     m22<T> R = rot(c, s);            // U_theta (column case) or V_theta (row case)
     if (p1) swap_rows(R);
@@ -156,13 +156,13 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
     T t2;
     bool t2inf = false;
     if (pos_eq(ra, rc)) {                                        // eq. (t2f'')
-        t2 = (T(2) * rc) / rb;
+        t2 = qdiv(T(2) * rc, rb);
         flags |= FL_T2F2;
     } else if (pos_eq(rb, rc)) {                                 // eq. (t2f''')
         t2 = ef_fl(ef_div(ef_mul(ef_pow2(1, erb), erc), ef_mul(era, era)));
         flags |= FL_T2F3;
-    } else if (pos_lt(ra / rb, fpt<T>::eps())) {                 // eq. (t2f''), only for t' ~ 13
-        t2 = (T(2) * rc) / rb;
+    } else if (pos_lt(qdiv(ra, rb), fpt<T>::eps())) {                 // eq. (t2f''), only for t' ~ 13
+        t2 = qdiv(T(2) * rc, rb);
         flags |= FL_T2F2;
     } else {                                               // eq. (t2f')
         T h = hypot_cr(ra, rb);
@@ -175,14 +175,14 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
     if (is_inf(t2)) t2inf = true;
     T tf;
     if (t2inf) { tf = T(1); flags |= FL_T2INF; }
-    else tf = t2 / (T(1) + hypot_cr(t2, T(1)));           // eq. (tf)
+    else tf = qdiv(t2, T(1) + hypot_cr(t2, T(1)));           // eq. (tf)
     T secf = hypot_cr(tf, T(1));
     z.tanphi = tf;
-    z.cphi = T(1) / secf;
-    z.sphi = tf / secf;
+    z.cphi = qdiv(T(1), secf);
+    z.sphi = qdiv(tf, secf);
     // Alg. 2
     T t = fma(rc, tf, rb);                                 // eq. (tp)
-    T tp = t / ra;
+    T tp = qdiv(t, ra);
     ef<T> s1, s2;
     if (is_inf(tp)) {                                       // eqs. (tp'), (s'')
         ef<T> et = ef_of(t);
@@ -194,8 +194,8 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
         flags |= FL_TPINF;
     } else {                                               // eq. (s')
         T secp = hypot_cr(tp, T(1));
-        z.cpsi = T(1) / secp;
-        z.spsi = tp / secp;
+        z.cpsi = qdiv(T(1), secp);
+        z.spsi = qdiv(tp, secp);
         ef<T> sf = ef_div(ef_of(secf), ef_of(secp));
         s1 = ef_div(era, sf);
         s2 = ef_mul(erc, sf);
@@ -282,25 +282,25 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
         bool pu = pos_lt(g11, g21);
         if (pu) { T x = g11; g11 = g21; g21 = x; x = g12; g12 = g22; g22 = x; }
         // eq. (QR15)
-        const T tth = g21 / g11;
+        const T tth = qdiv(g21, g11);
         const T secth = hypot_cr(tth, T(1));
         T r11 = w1, r12, r22;
         if (eq0(fma(tth, g11, ngt(g21)))) {                // tan(theta) exact: Lemma 3.4
-            r12 = fma(g22, tth, g12) / secth;
-            r22 = fma(ngt(g12), tth, g22) / secth;
+            r12 = qdiv(fma(g22, tth, g12), secth);
+            r22 = qdiv(fma(ngt(g12), tth, g22), secth);
         } else if (lt0(g12) == lt0(g22)) {         // Thm. 3.5: r22 by eq. (EXT)
-            r12 = fma(g22, tth, g12) / secth;
-            r22 = ext_num_div(g22, g11, g12, g21, true, g11) / secth;
+            r12 = qdiv(fma(g22, tth, g12), secth);
+            r22 = qdiv(ext_num_div(g22, g11, g12, g21, true, g11), secth);
             flags |= FL_EXT;
         } else {                                           // Thm. 3.5: r12 by eq. (EXT)
-            r22 = fma(ngt(g12), tth, g22) / secth;
-            r12 = ext_num_div(g12, g11, g22, g21, false, g11) / secth;
+            r22 = qdiv(fma(ngt(g12), tth, g22), secth);
+            r12 = qdiv(ext_num_div(g12, g11, g22, g21, false, g11), secth);
             flags |= FL_EXT;
         }
         if (eq0(r12) || eq0(r22)) {
             // R'' of type 9 (or 1) or 5: finish as Sect. 3.1, G' = S1 P_U U_theta R'' P_V^T
             flags |= FL_FALLBACK;
-            const T cth = T(1) / secth, sth = tth / secth;
+            const T cth = qdiv(T(1), secth), sth = qdiv(tth, secth);
             m22<T> Ur, Vr;
             if (eq0(r12)) {
                 simple9<T>(!eq0(r22) ? 9 : 1, r11, T(0), T(0), r22, Ur, Vr, d1, d2);
@@ -336,17 +336,17 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
             o.V = V;
             // U = S1 P_U S22 U(phi +- theta) S2 P_sigma: eqs. (p+t), (p-t), (tan+-), (UV)
             const bool plus = !n22;
-            const T tb = z.swap ? T(1) / z.tanpsi : z.tanphi;
+            const T tb = z.swap ? qdiv(T(1), z.tanpsi) : z.tanphi;
             T ca, sa;
             if (is_inf(tb)) {
-                const T cth = T(1) / secth, sth = tth / secth;
+                const T cth = qdiv(T(1), secth), sth = qdiv(tth, secth);
                 ca = plus ? ngt(sth) : sth; sa = cth;
             } else {
                 const T N = plus ? tb + tth : tb - tth;
                 const T D = plus ? fma(ngt(tb), tth, T(1)) : fma(tb, tth, T(1));
                 if (eq0(D)) { ca = T(0); sa = lt0(N) ? T(-1) : T(1); }
                 else {
-                    const T ta = N / D;
+                    const T ta = qdiv(N, D);
                     if (is_inf(ta)) { ca = T(0); sa = lt0(N) ? T(-1) : T(1); }
                     else {
                         T c0, s0;
