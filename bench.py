@@ -47,8 +47,9 @@ def parse():
     p.add_argument("--no-fp32", action="store_true")
     p.add_argument("--no-fwd-bwd", action="store_true")
     p.add_argument("--no-kog", action="store_true")
-    p.add_argument("--profile-case", choices=["d", "s"], default=None,
-                   help="run a small case of the 2x2 kernels (for ncu captures) and exit")
+    p.add_argument("--profile-case", choices=["d", "s", "kog"], default=None,
+                   help="run a small case of the 2x2 kernels or of the persistent Kogbetliantz "
+                        "kernel (for ncu captures) and exit")
     p.add_argument("--profile-n", type=int, default=1 << 22)
     return p.parse_args()
 
@@ -143,8 +144,8 @@ class Clocks:
 # dram__bytes_write.sum) of `python bench.py --profile-case d` (2^22 matrices), scaled by
 # the matrix count to a full 2^27-matrix launch.  Valid only for the kernel sources with
 # this hash; any change to them reports null until a new capture is taken.
-TRAFFIC_SRC_HASH = "ad1bb78823a8a59f"
-TRAFFIC_BYTES_PER_MATRIX = (135.570176e6 + 277.161728e6) / (1 << 22)
+TRAFFIC_SRC_HASH = "49cafbc260a2b3e2"
+TRAFFIC_BYTES_PER_MATRIX = (134.309120e6 + 293.176064e6) / (1 << 22)
 KERNEL_SOURCES = ("k2_fp.cuh", "k2_svd2.cuh", "k2_gesvd2.cu")
 
 
@@ -550,11 +551,22 @@ def run_reference(a):
 
 def profile_case(a):
     """A few launches of each 2x2 kernel on a small batch of the wide-range workload
-    (2^22 matrices by default: 470 MB of inputs and outputs in double, above L2)."""
+    (2^22 matrices by default: 470 MB of inputs and outputs in double, above L2), or one
+    persistent Kogbetliantz run over 304 FP64 matrices of the batched workload's order mix
+    (default block sizes, no graph: one launch per order bucket)."""
     import torch
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
     dev = torch.device("cuda", 0)
+    if a.profile_case == "kog":
+        orders = I.kog_orders(304, 8, 128, SEED + 4)
+        flat, _ = I.kog_batch(orders, SEED + 4)
+        A = torch.from_numpy(flat).to(dev)
+        U, S, V, sw, info = k2svd.kogbet(A, orders, flags=k2svd.KOG_NOTUNE)
+        torch.cuda.synchronize()
+        print("profile case kog: %d matrices, mean sweeps %.2f, converged %d" %
+              (len(orders), sw.double().mean().item(), int((info == 0).sum().item())))
+        return
     n = a.profile_n
     G = I.general(n, SEED + 2, a.profile_case, "wide", xp="torch", device=dev)
     T3 = I.triangular(n, SEED + 3, a.profile_case, "wide", xp="torch", device=dev)
