@@ -5,11 +5,21 @@
 // Persistent form: the matrices are grouped by order into buckets.  Each bucket is one
 // persistent launch: every CTA takes the next matrix from a queue (largest first) and runs
 // all of its sweeps alone, with G in shared memory (orders up to 128 double / 224 float)
-// or in the workspace.  A step is three phases separated by block barriers: the pivot
-// SVDs (one thread per pivot), the row rotations (pair index fastest, so that a warp reads
-// consecutive rows), the column rotations with the U and V updates and the pivot blocks
-// (row index fastest).  The off-norm is summed column by column in a fixed order, so the
-// sweep count -- and every bit of the result -- does not depend on the launch shape.
+// or in the workspace.  A step k is two phases separated by block barriers:
+//   1. G <- U-hat^T G V-hat: every thread takes 2x2 blocks (rows of one pivot pair or
+//      unpaired index, columns of another) and applies the row rotation, then the column
+//      rotation -- the same operations, in the same order, as rotating all rows first and
+//      all columns second; diagonal pivot blocks become diag(sigma1, sigma2);
+//   2. the U and V updates of step k.
+// The pivot SVDs of step k+1 overlap both: before phase 1, the pivot threads (the first
+// warps, one thread per pivot) compute the four elements of their pivot in G_{k+1} from
+// G_k and the rotations of step k -- the same operations phase 1 applies to them -- and
+// after a barrier they run the SVDs while the remaining warps do phases 1 and 2.  The long
+// serial 2x2 SVDs thus hide behind the FP64 rotation work.  Blocks too small to spare a
+// warp run the phases one after the other.  The pivot parameters are double buffered and
+// stored by parameter (stride nmax/2+1), so a warp reads them without bank conflicts.
+// The off-norm is summed column by column in a fixed order, so the sweep count -- and
+// every bit of the result -- does not depend on the launch shape.
 //
 // Per-step form (K2SVD_KOG_PLAIN): G in the workspace, three launches per step over the
 // whole batch, and a host read-back per sweep for the convergence test.
@@ -47,13 +57,16 @@ template <typename T> struct kog_params {
     int nmax;              // largest order of the launch (shared-memory capacity)
 };
 
-template <typename T> __host__ __device__ constexpr size_t kog_piv_elems(int nmax) { return (size_t)(nmax / 2 + 1) * 10; }
+// pivot parameters of one step: 10 values for each of at most nmax/2 pivots, stored by
+// parameter with stride kog_piv_stride; two such buffers
+__host__ __device__ constexpr int kog_piv_stride(int nmax) { return nmax / 2 + 1; }
+template <typename T> __host__ __device__ constexpr size_t kog_piv_elems(int nmax) { return (size_t)kog_piv_stride(nmax) * 10; }
 
 template <typename T>
 __host__ __device__ inline size_t kog_smem_bytes(int nmax, bool gg)
 {
     size_t g = gg ? 0 : (size_t)(nmax + 1) * nmax * sizeof(T);
-    return g + kog_piv_elems<T>(nmax) * sizeof(T) + (size_t)nmax * sizeof(T) + 2 * (size_t)nmax * sizeof(int) + 64;
+    return g + 2 * kog_piv_elems<T>(nmax) * sizeof(T) + (size_t)nmax * sizeof(T) + 2 * (size_t)nmax * sizeof(int) + 64;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -98,38 +111,123 @@ __device__ int kog_load(const T *A, T *G, int ld, T *U, T *V, int n, kog_sh *sh)
     return k;
 }
 
-// One step (pivot SVDs, rows, columns + U + V + pivot blocks) on G with leading dimension ld.
+// Pivot SVDs of step st from G into piv (stride ps), by threads t0, t0+tn, ...
 template <typename T>
-__device__ __forceinline__ void kog_step(T *G, int ld, T *U, T *V, int n, int st, T *piv)
+__device__ __forceinline__ void kog_pivots(const T *G, int ld, int n, int st, T *piv, int ps, int t0, int tn)
 {
     const int np = modulus_count(n, st);
-    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    for (int p = t0; p < np; p += tn) {
         int i, j;
         modulus_pair(n, st, p, i, j);
-        kog_pivot(G[(size_t)i * ld + i], G[(size_t)i * ld + j], G[(size_t)j * ld + i], G[(size_t)j * ld + j], piv + 10 * p);
+        kog_pivot(G[(size_t)i * ld + i], G[(size_t)i * ld + j], G[(size_t)j * ld + i], G[(size_t)j * ld + j],
+                  piv + p, ps);
     }
-    __syncthreads();
+}
+
+// Phase 1 of step st: G <- U-hat^T G V-hat by 2x2 blocks.  Block (a, b) has the rows of
+// group a and the columns of group b, a group being a pivot pair (a < np) or an unpaired
+// index.  Each element gets the row rotation first, then the column rotation.
+template <typename T>
+__device__ __forceinline__ void kog_rotate_g(T *G, int ld, int n, int st, const T *piv, int ps, int t0, int tn)
+{
+    const int np = modulus_count(n, st), nq = n - np;          // groups: np pairs + (n - 2 np) singles
+    const int items = nq * nq;
+    for (int w = t0; w < items; w += tn) {
+        const int a = w % nq, b = w / nq;
+        int ia, ja = -1, ib, jb = -1;
+        if (a < np) modulus_pair(n, st, a, ia, ja); else ia = modulus_single(n, st, a - np);
+        if (b < np) modulus_pair(n, st, b, ib, jb); else ib = modulus_single(n, st, b - np);
+        if (ja < 0 && jb < 0) continue;                        // unpaired row and column
+        if (a == b) {                                // the pivot block -> diag(sigma)
+            G[(size_t)ia * ld + ia] = piv[8 * ps + a];
+            G[(size_t)ia * ld + ja] = T(0);
+            G[(size_t)ja * ld + ia] = T(0);
+            G[(size_t)ja * ld + ja] = piv[9 * ps + a];
+            continue;
+        }
+        T *c0 = G + (size_t)ib * ld, *c1 = jb >= 0 ? G + (size_t)jb * ld : nullptr;
+        T x00 = c0[ia], x10 = T(0), x01 = T(0), x11 = T(0);
+        if (ja >= 0) x10 = c0[ja];
+        if (jb >= 0) { x01 = c1[ia]; if (ja >= 0) x11 = c1[ja]; }
+        if (ja >= 0) {                                         // rows ia, ja <- U-hat^T
+            rot2(x00, x10, piv + a, ps);
+            if (jb >= 0) rot2(x01, x11, piv + a, ps);
+        }
+        if (jb >= 0) {                                         // columns ib, jb <- V-hat
+            rot2(x00, x01, piv + 4 * ps + b, ps);
+            if (ja >= 0) rot2(x10, x11, piv + 4 * ps + b, ps);
+        }
+        c0[ia] = x00;
+        if (ja >= 0) c0[ja] = x10;
+        if (jb >= 0) { c1[ia] = x01; if (ja >= 0) c1[ja] = x11; }
+    }
+}
+
+// U and V updates of step st (columns i, j of U <- U-hat, of V <- V-hat) by threads
+// t0, t0+tn, ...
+template <typename T>
+__device__ __forceinline__ void kog_rotate_uv(T *U, T *V, int n, int st, const T *piv, int ps, int t0, int tn)
+{
+    const int np = modulus_count(n, st);
     const int items = np * n;
-    for (int w = threadIdx.x; w < items; w += blockDim.x) {          // rows i, j <- U-hat^T
-        const int p = w % np, c = w / np;
-        int i, j;
-        modulus_pair(n, st, p, i, j);
-        rot2(G[(size_t)c * ld + i], G[(size_t)c * ld + j], piv + 10 * p);
-    }
-    __syncthreads();
-    for (int w = threadIdx.x; w < items; w += blockDim.x) {          // columns i, j <- V-hat
+    for (int w = t0; w < items; w += tn) {
         const int r = w % n, p = w / n;
         int i, j;
         modulus_pair(n, st, p, i, j);
-        const T *m = piv + 10 * p;
-        if (r == i || r == j) {
-            G[(size_t)i * ld + r] = (r == i) ? m[8] : T(0);
-            G[(size_t)j * ld + r] = (r == j) ? m[9] : T(0);
-        } else {
-            rot2(G[(size_t)i * ld + r], G[(size_t)j * ld + r], m + 4);
+        rot2(U[(size_t)i * n + r], U[(size_t)j * n + r], piv + p, ps);
+        rot2(V[(size_t)i * n + r], V[(size_t)j * n + r], piv + 4 * ps + p, ps);
+    }
+}
+
+// Element (r, c) of G_{k+1} computed from G_k and the rotations of step st, with the
+// operations phase 1 applies to it: the row rotation of r's pair (both columns of c's
+// group), then the column rotation of c's pair; sigma or zero inside a pivot block.
+template <typename T>
+__device__ __forceinline__ T kog_next_entry(const T *G, int ld, int n, int st, const T *piv, int ps, int r, int c)
+{
+    int ia, ja, ib, jb;
+    const int a = modulus_group(n, st, r, ia, ja), b = modulus_group(n, st, c, ib, jb);
+    if (a >= 0 && a == b) return r == c ? piv[(r == ia ? 8 : 9) * ps + a] : T(0);
+    auto g1 = [&](int x) -> T {                        // row-rotated element (r, x)
+        if (a < 0) return G[(size_t)x * ld + r];
+        const T u = G[(size_t)x * ld + ia], v = G[(size_t)x * ld + ja];
+        return r == ia ? fma(piv[ps + a], v, piv[a] * u) : fma(piv[3 * ps + a], v, piv[2 * ps + a] * u);
+    };
+    if (b < 0) return g1(c);
+    const T x = g1(ib), y = g1(jb);
+    return c == ib ? fma(piv[5 * ps + b], y, piv[4 * ps + b] * x) : fma(piv[7 * ps + b], y, piv[6 * ps + b] * x);
+}
+
+// One step st of the persistent form (parameters in pc), leaving the pivot parameters of
+// step nx in pn.  Ends with a block barrier.
+template <typename T>
+__device__ __forceinline__ void kog_step(T *G, int ld, T *U, T *V, int n, int st, int nx, const T *pc, T *pn, int ps)
+{
+    const int npn = modulus_count(n, nx);
+    const int w0 = (npn + 31) & ~31;
+    const int tid = threadIdx.x;
+    if ((int)blockDim.x - w0 >= 32) {
+        T g11 = T(0), g21 = T(0), g12 = T(0), g22 = T(0);
+        if (tid < npn) {
+            int i, j;
+            modulus_pair(n, nx, tid, i, j);
+            g11 = kog_next_entry(G, ld, n, st, pc, ps, i, i);
+            g21 = kog_next_entry(G, ld, n, st, pc, ps, j, i);
+            g12 = kog_next_entry(G, ld, n, st, pc, ps, i, j);
+            g22 = kog_next_entry(G, ld, n, st, pc, ps, j, j);
         }
-        rot2(U[(size_t)i * n + r], U[(size_t)j * n + r], m);
-        rot2(V[(size_t)i * n + r], V[(size_t)j * n + r], m + 4);
+        __syncthreads();                                    // G_k read before phase 1 writes
+        if (tid < w0) {
+            if (tid < npn) kog_pivot(g11, g21, g12, g22, pn + tid, ps);
+        } else {
+            kog_rotate_g(G, ld, n, st, pc, ps, tid - w0, blockDim.x - w0);
+            kog_rotate_uv(U, V, n, st, pc, ps, tid - w0, blockDim.x - w0);
+        }
+    } else {
+        kog_rotate_g(G, ld, n, st, pc, ps, tid, blockDim.x);
+        __syncthreads();
+        kog_rotate_uv(U, V, n, st, pc, ps, tid, blockDim.x);
+        kog_pivots(G, ld, n, nx, pn, ps, tid, blockDim.x);
     }
     __syncthreads();
 }
@@ -191,7 +289,8 @@ __global__ void __launch_bounds__(512) kog_persistent(const kog_params<T> P)
     __shared__ kog_sh sh;
     T *Gs = reinterpret_cast<T *>(smem);
     T *piv = Gs + (GG ? 0 : (size_t)(P.nmax + 1) * P.nmax);
-    T *colsum = piv + kog_piv_elems<T>(P.nmax);
+    const int ps = kog_piv_stride(P.nmax);
+    T *colsum = piv + 2 * kog_piv_elems<T>(P.nmax);
     int *perm = reinterpret_cast<int *>(colsum + P.nmax);
     for (;;) {
         if (threadIdx.x == 0) sh.slot = atomicAdd(P.queue, 1);
@@ -218,10 +317,22 @@ __global__ void __launch_bounds__(512) kog_persistent(const kog_params<T> P)
         const T tol = (T(P.tol_factor) * T(n)) * kog_eps<T>::v() * nrm;
         T off = kog_norm(G, n, ld, true, colsum, bc);
         int sw = 0;
-        while (!(off < tol) && sw < P.max_sweeps && off > T(0)) {
-            for (int st = 0; st < n; ++st) kog_step(G, ld, U, V, n, st, piv);
+        bool go = !(off < tol) && sw < P.max_sweeps && off > T(0);
+        T *pc = piv, *pn = piv + kog_piv_elems<T>(P.nmax);
+        if (go) {
+            kog_pivots(G, ld, n, 0, pc, ps, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
+        while (go) {
+            for (int st = 0; st < n; ++st) {
+                // the pivots of the next step: step 0 of the next sweep after the last one
+                // (unused when the sweeps end)
+                kog_step(G, ld, U, V, n, st, st + 1 < n ? st + 1 : 0, pc, pn, ps);
+                T *t = pc; pc = pn; pn = t;
+            }
             ++sw;
             off = kog_norm(G, n, ld, true, colsum, bc);
+            go = !(off < tol) && sw < P.max_sweeps && off > T(0);
         }
         kog_finish(G, ld, U, V, S, n, k, colsum, perm, G);
         if (threadIdx.x == 0) {
@@ -483,7 +594,7 @@ struct tune_key {
 static std::mutex g_mu;
 static std::map<tune_key, int> g_tuned;
 
-static int default_threads(int nmax) { return nmax <= 32 ? 128 : (nmax <= 64 ? 256 : 512); }
+static int default_threads(int nmax) { return nmax <= 32 ? 64 : (nmax <= 64 ? 256 : 512); }
 
 template <typename T, bool GG>
 static cudaError_t launch_bucket(const kog_params<T> &P, int threads, cudaStream_t st, int *queue_dev)
@@ -541,7 +652,7 @@ static int autotune(const kog_plan<T> &pl, const kog_params<T> &base, cudaStream
             if (it != g_tuned.end()) { threads[b] = it->second; continue; }
         }
         if (!tune) continue;
-        const int cand[3] = {128, 256, 512};
+        const int cand[5] = {32, 64, 128, 256, 512};
         kog_params<T> P = base;
         P.desc = reinterpret_cast<const kog_desc *>(ws + pl.off_desc) + pl.bstart[b];
         P.count = std::min(cnt, 2 * sms);
