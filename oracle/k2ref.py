@@ -66,6 +66,7 @@ def lib():
                 T = D if sfx == "d" else F
                 fn = getattr(L, "k2ref_hypot_" + sfx)
                 fn.argtypes = [T, T]
+                getattr(L, "k2ref_hypot_n_" + sfx).argtypes = [I64, P, P, P, C.c_int]
                 fn.restype = T
                 getattr(L, "k2ref_trace_" + sfx).argtypes = [P, P, P]
                 getattr(L, "k2ref_efops_" + sfx).argtypes = [T, T, P, P]
@@ -142,6 +143,15 @@ def trsvd2(F, Gp, H, prec="d", nthreads=1):
 def hypot(x, y, prec="d"):
     """Correctly rounded hypot (Sect. 2)."""
     return getattr(lib(), "k2ref_hypot_" + prec)(x, y)
+
+
+def hypot_n(x, y, prec="d", nthreads=1):
+    """Correctly rounded hypot (Sect. 2) of arrays x, y, elementwise."""
+    T = _dt(prec)
+    x = np.ascontiguousarray(x, dtype=T); y = np.ascontiguousarray(y, dtype=T)
+    h = np.empty_like(x)
+    getattr(lib(), "k2ref_hypot_n_" + prec)(x.size, _ptr(x), _ptr(y), _ptr(h), int(nthreads))
+    return h
 
 
 def trace(g, prec="d"):

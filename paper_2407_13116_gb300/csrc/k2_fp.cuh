@@ -305,72 +305,87 @@ template <typename T> __device__ __forceinline__ ef<T> ef_minus(T x, T y)
 }
 
 // ---------------------------------------------------------------------------------------
+// floor(sqrt(X)) for an integer X in [2^110, 2^113), and the remainder X - floor(sqrt(X))^2,
+// on the integer pipes (Newton's method for the square root):
+//   * s0 = sqrt(X) (1 + e), |e| < 2^-21.4, from the FP32 reciprocal square root y of the
+//     leading 31 bits of X (rsqrtf is within 2 ulp);
+//   * two corrections s <- s + (X - s^2) / (2 s): the residual is exact in 128-bit
+//     integers, the quotient R y / 2 is formed in FP32 from its leading bits and rounded to
+//     an integer.  Each error bound: |s1 - sqrt X| < 2^14.2 (Newton's quadratic term
+//     e0^2 / 2 s0) + 2^14.8 (the FP32 quotient, 2^-20.3 relative of |e0| < 2^35.1) + 1/2,
+//     then |s2 - sqrt X| < 1/2 + 2^-4.7;
+//   * floor(sqrt X) is s2 or s2 - 1, decided by the sign of X - s2^2.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t isqrt113(u128 X, u128 &rem)
+{
+    const float xf = __uint2float_rz((uint32_t)(X >> 82));           // [2^28, 2^31)
+    const float y = rsqrtf(xf);                                       // 2^41 / sqrt(X), within 2^-21.6
+    uint64_t s = (uint64_t)__float2ull_rn(xf * y * 0x1p41f);
+    __int128 R = (__int128)(X - (u128)s * s);                         // |R| < 2^93
+    s += (uint64_t)__float2ll_rn(__ll2float_rn((long long)(R >> 40)) * y * 0x1p-2f);
+    R = (__int128)(X - (u128)s * s);                                  // |R| < 2^73.2
+    s += (uint64_t)__float2ll_rn(__ll2float_rn((long long)(R >> 16)) * y * 0x1p-26f);
+    R = (__int128)(X - (u128)s * s);
+    if (R < 0) { R += (__int128)(2 * s) - 1; s -= 1; }
+    rem = (u128)R;
+    return s;
+}
+
+// ---------------------------------------------------------------------------------------
 // Correctly rounded hypot (Sect. 2).  With a = max(|x|,|y|), b = min:
 //  * e_a - e_b >= (p+1)/2: b^2 < a ulp(a), so sqrt(a^2+b^2) lies strictly inside
 //    (a, a + ulp(a)/2) and rounds to a;
-//  * a subnormal: both are integers times the smallest subnormal q, the result is
-//    round(sqrt(A^2+B^2)) q (no ties: 4N is even, (2k+1)^2 odd);
-//  * otherwise a candidate r = sqrt(fma(a', a', b'*b')) of the operands scaled to a' in
-//    [1,2) is within two steps of the result; it is corrected by comparing the exact
-//    a'^2 + b'^2 with the squared midpoints to the neighbouring values, in integers
-//    (units 2^-110 for double, 2^-52 for float), ties to even.
+//  * otherwise the exact sum of squares X is formed as an integer (a' = a scaled to
+//    [1,2), units 2^-110 for double; both subnormal: units of the smallest subnormal
+//    squared) and the result is rounded from floor(sqrt X) and the remainder, ties to
+//    even.  The double version uses no FP64 instruction on this path.  For float, a
+//    candidate sqrt(fma(a', a', b'*b')) is corrected by comparing the exact a'^2 + b'^2 with
+//    the squared midpoints to the neighbouring values, in integers (units 2^-52).
 // ---------------------------------------------------------------------------------------
 static __device__ __noinline__ double hypot_cr(double x, double y)
 {
-    double a = fabs(x), b = fabs(y);
-    if (a < b) { double t = a; a = b; b = t; }
-    if (!(a <= 0x1.fffffffffffffp1023)) return a + b;     // inf or nan
-    if (b == 0.0) return a;
-    uint64_t ab = dbits(a), bb = dbits(b);
-    int Ea = (int)(ab >> 52), Eb = (int)(bb >> 52);
+    uint64_t ab = dbits(x) & ~D_SIGN, bb = dbits(y) & ~D_SIGN;
+    if (ab < bb) { uint64_t t = ab; ab = bb; bb = t; }
+    if ((ab >> 52) == 0x7FF) return dfrom(ab) + dfrom(bb);    // inf or nan
+    if (bb == 0) return dfrom(ab);
+    const int Ea = (int)(ab >> 52), Eb = (int)(bb >> 52);
     uint64_t A = ab & D_MANT, B = bb & D_MANT;
     int ea, eb;
     if (Ea) { A |= D_HID; ea = Ea - 1023; } else { int sh = __clzll((long long)A) - 11; A <<= sh; ea = -1022 - sh; }
     if (Eb) { B |= D_HID; eb = Eb - 1023; } else { int sh = __clzll((long long)B) - 11; B <<= sh; eb = -1022 - sh; }
-    if (ea - eb >= 27) return a;
+    if (ea - eb >= 27) return dfrom(ab);
+    u128 rem;
     if (Ea == 0) {
-        u128 N = (u128)ab * ab + (u128)bb * bb;                 // units of 2^-2148
-        double nd = __ull2double_rn((unsigned long long)(N >> 41)) * 0x1p41;
-        uint64_t q = (uint64_t)__double2ull_rn(sqrt(nd));
-        u128 N4 = N << 2;
-#pragma unroll 1
-        for (int it = 0; it < 4; ++it) {
-            u128 hi = (u128)(2 * q + 1) * (2 * q + 1);
-            if (hi < N4) { ++q; continue; }
-            u128 lo = (u128)(2 * q - 1) * (2 * q - 1);
-            if (q > 0 && lo > N4) { --q; continue; }
-            break;
-        }
-        return dfrom(q);                                       // q * 2^-1074, q < 2^53
+        // both subnormal: N = (a^2 + b^2) / q^2 with q = 2^-1074 (N < 2^105), the result
+        // round(sqrt N) q; no ties (4N is even, (2k+1)^2 odd)
+        const u128 N = (u128)ab * ab + (u128)bb * bb;
+        const int k = (111 - (127 - clz128(N))) >> 1;               // N 4^k in [2^110, 2^113)
+        uint64_t q = isqrt113(N << (2 * k), rem) >> k;              // floor(sqrt N)
+        if (N - (u128)q * q > q) ++q;                               // sqrt N > q + 1/2
+        return dfrom(q);                                            // q < 2^53
     }
-    double as = dfrom((1023ull << 52) | (A & D_MANT));
-    double bs = dfrom(((uint64_t)(eb - ea + 1023) << 52) | (B & D_MANT));
-    double r = sqrt(fma(as, as, bs * bs));
     // exact a'^2 + b'^2 in units of 2^-110, with a sticky bit for truncated bits of b'^2
     u128 X = ((u128)A * A) << 6;
-    u128 B2 = (u128)B * B;
-    int sh = 2 * (eb - ea) + 6;
+    const u128 B2 = (u128)B * B;
+    const int sh = 2 * (eb - ea) + 6;
     bool sticky = false;
     if (sh >= 0) X += B2 << sh;
-    else { int k = -sh; sticky = (B2 << (128 - k)) != 0; X += B2 >> k; }
-#pragma unroll 1
-    for (int it = 0; it < 4; ++it) {
-        uint64_t rb = dbits(r);
-        int er = (int)(rb >> 52) - 1023;                       // 0 or 1
-        uint64_t R = (rb & D_MANT) | D_HID;
-        u128 Mhi = ((u128)(2 * R + 1) * (2 * R + 1)) << (2 * er + 4);
-        if (X > Mhi || (X == Mhi && sticky)) { r = dfrom(rb + 1); continue; }
-        if (X == Mhi) { if (R & 1) r = dfrom(rb + 1); break; }
-        u128 Mlo = (R == D_HID) ? (((u128)(4 * R - 1) * (4 * R - 1)) << (2 * er + 2))
-                                : (((u128)(2 * R - 1) * (2 * R - 1)) << (2 * er + 4));
-        if (X < Mlo) { r = dfrom(rb - 1); continue; }
-        if (X == Mlo && !sticky && (R & 1)) r = dfrom(rb - 1);
-        break;
+    else { const int k = -sh; sticky = (B2 << (128 - k)) != 0; X += B2 >> k; }
+    // sqrt(X 2^-110) = sqrt(X) 2^-55 in [1, 2 sqrt 2): 53 bits of floor(sqrt X), round bit,
+    // sticky from the lower bits, the remainder and the truncated b'^2
+    const uint64_t s = isqrt113(X, rem);
+    const int er = (s >> 56) ? 1 : 0;
+    const int cut = 3 + er;
+    uint64_t R = s >> cut;
+    const bool rb = (s >> (cut - 1)) & 1;
+    const bool st = (s & ((1ull << (cut - 1)) - 1)) != 0 || rem != 0 || sticky;
+    int E = ea + er + 1023;
+    if (rb && (st || (R & 1))) {
+        ++R;
+        if (R >> 53) { R >>= 1; ++E; }
     }
-    uint64_t rb = dbits(r);
-    int E = (int)(rb >> 52) + ea;                              // biased exponent of the result
     if (E >= 2047) return dfrom(0x7FFull << 52);
-    return dfrom(((uint64_t)E << 52) | (rb & D_MANT));
+    return dfrom(((uint64_t)E << 52) | (R & D_MANT));
 }
 
 static __device__ __noinline__ float hypot_cr(float x, float y)

@@ -1,8 +1,10 @@
 """The two correctly rounded primitives of the 2x2 kernels, checked on the device:
 the integer-pipe binary64 division against the FP64 divider (IEEE division, correctly
 rounded by definition) on about 1.3e9 operand pairs, and hypot against the oracle's exact
-midpoint hypot on a sample."""
+midpoint hypot on 2.5e7 pairs, exact ties and special operands."""
 import ctypes as C
+import math
+import os
 
 import numpy as np
 import pytest
@@ -85,15 +87,67 @@ def test_division_special_operands():
     assert bool(same.all())
 
 
-def test_hypot_matches_oracle_sample():
-    L = _lib()
-    gen = torch.Generator(device=DEV).manual_seed(7)
-    n = 1 << 16
-    a = torch.cat([_bits_double(n, gen, -1022, 1023, 0.05), _bits_double(n, gen, -30, 30)])
-    b = torch.cat([_bits_double(n, gen, -1022, 1023, 0.05), _bits_double(n, gen, -40, 30)])
+def _hyp(L, a, b):
     h = torch.empty_like(a)
     assert L.k2probe_hypot(a.numel(), a.data_ptr(), b.data_ptr(), h.data_ptr(),
                            torch.cuda.current_stream().cuda_stream) == 0
-    an, bn, hn = a.cpu().numpy(), b.cpu().numpy(), h.cpu().numpy()
-    for i in range(0, len(an), 7):
-        assert hn[i] == oracle.hypot(float(an[i]), float(bn[i])), (an[i], bn[i])
+    return h
+
+
+def _check_hypot(a, b, h):
+    an, bn = a.cpu().numpy(), b.cpu().numpy()
+    ref = oracle.hypot_n(an, bn, "d", nthreads=os.cpu_count() or 1)
+    got = h.cpu().numpy()
+    bad = got.view(np.int64) != ref.view(np.int64)
+    assert not bad.any(), (an[bad][:4].tolist(), bn[bad][:4].tolist(), got[bad][:4].tolist(), ref[bad][:4].tolist())
+
+
+@pytest.mark.parametrize("case", ["full", "narrow", "ratio_edge", "subnormal", "overflow", "near_one_to_two"])
+def test_hypot_matches_oracle(case):
+    """2^22 pairs per case, every result compared with the oracle's hypot (exact midpoint
+    tests on big integers)."""
+    L = _lib()
+    gen = torch.Generator(device=DEV).manual_seed(7 + (hash(case) & 0xFF))
+    n = 1 << 22
+    if case == "full":
+        a, b = _bits_double(n, gen, -1022, 1023, 0.05), _bits_double(n, gen, -1022, 1023, 0.05)
+    elif case == "narrow":
+        a, b = _bits_double(n, gen, -30, 30), _bits_double(n, gen, -40, 30)
+    elif case == "ratio_edge":           # exponent differences around the (p+1)/2 = 27 cut
+        a = _bits_double(n, gen, -100, 100)
+        d = torch.randint(20, 31, (n,), generator=gen, device=DEV, dtype=torch.int64)
+        b = (_bits_double(n, gen, 0, 0).view(torch.int64) + ((a.view(torch.int64) >> 52 & 0x7FF) - 1023 - d << 52)).view(torch.float64)
+    elif case == "subnormal":
+        a, b = _bits_double(n, gen, -1022, -1000, 0.6), _bits_double(n, gen, -1022, -1000, 0.6)
+    elif case == "overflow":
+        a, b = _bits_double(n, gen, 1018, 1023), _bits_double(n, gen, 1010, 1023)
+    else:                                # a', b' both near 2: sums of squares near 2^113
+        a = _bits_double(n, gen, 0, 0)
+        a = (a.view(torch.int64) | (0xFFFFF << 32)).view(torch.float64)
+        b = (a.view(torch.int64) - torch.randint(0, 1 << 30, (n,), generator=gen, device=DEV, dtype=torch.int64)).view(torch.float64)
+    _check_hypot(a, b, _hyp(L, a, b))
+
+
+def test_hypot_exact_ties_and_specials():
+    """Pythagorean triples whose hypotenuse is a midpoint between two doubles (ties to
+    even), exact triples, and zero / infinite / NaN / extreme operands."""
+    import random
+    from test_oracle_hypot import _euclid_ties
+    L = _lib()
+    xs, ys = [], []
+    for (p, q, c) in _euclid_ties(53, 200, random.Random(5)):
+        for sc in (0, -540, 600, -1000, 960):
+            xs += [math.ldexp(p, sc), math.ldexp(q, sc)]
+            ys += [math.ldexp(q, sc), -math.ldexp(p, sc)]
+    for k in range(-1070, 1020, 7):
+        xs.append(math.ldexp(3.0, k)); ys.append(math.ldexp(4.0, k))
+    sp = [0.0, -0.0, 5e-324, -5e-324, 2.2250738585072014e-308, 1.0, 1.7976931348623157e308, float("inf"), float("-inf")]
+    for u in sp:
+        for v in sp:
+            xs.append(u); ys.append(v)
+    a = torch.tensor(xs, dtype=torch.float64, device=DEV)
+    b = torch.tensor(ys, dtype=torch.float64, device=DEV)
+    _check_hypot(a, b, _hyp(L, a, b))
+    u = torch.tensor([float("nan"), 1.0, float("nan"), 0.0], dtype=torch.float64, device=DEV)
+    v = torch.tensor([1.0, float("nan"), float("nan"), float("nan")], dtype=torch.float64, device=DEV)
+    assert bool(torch.isnan(_hyp(L, u, v)).all())
