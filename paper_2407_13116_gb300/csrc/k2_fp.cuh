@@ -53,6 +53,8 @@ __device__ __forceinline__ bool is_fin(float x) { return ((fbits(x) >> 23) & 0xF
 __device__ __forceinline__ bool abs_lt(double a, double b) { return (dbits(a) << 1) < (dbits(b) << 1); }
 __device__ __forceinline__ bool abs_lt(float a, float b) { return (fbits(a) << 1) < (fbits(b) << 1); }
 // -0 -> +0, anything else unchanged
+__device__ __forceinline__ double absv(double x) { return dfrom(dbits(x) & ~D_SIGN); }
+__device__ __forceinline__ float absv(float x) { return ffrom(fbits(x) & ~F_SIGN); }
 __device__ __forceinline__ double unneg0(double x) { uint64_t b = dbits(x); return dfrom(b == D_SIGN ? 0 : b); }
 __device__ __forceinline__ float unneg0(float x) { uint32_t b = fbits(x); return ffrom(b == F_SIGN ? 0u : b); }
 
@@ -87,7 +89,7 @@ template <> struct fpt<double> {
     // f * 2^e rounded once; f = 0 or 1 <= |f| < 2
     __device__ static __forceinline__ double ldexp_rn(double f, int e)
     {
-        if (f == 0.0) return f;
+        if (eq0(f)) return f;
         uint64_t b = dbits(f), keep = b & (D_SIGN | D_MANT);
         if (e > 1023) return dfrom((b & D_SIGN) | (0x7FFull << 52));
         if (e >= -1022) return dfrom(keep | ((uint64_t)(e + 1023) << 52));
@@ -99,7 +101,7 @@ template <> struct fpt<double> {
     // x 2^s rounded once, any finite x
     __device__ static __forceinline__ double scale(double x, int s)
     {
-        if (x == 0.0) return x;
+        if (eq0(x)) return x;
         int e; double f; split(x, e, f);
         return ldexp_rn(f, e + s);
     }
@@ -128,7 +130,7 @@ template <> struct fpt<float> {
     __device__ static __forceinline__ int expo(float x) { int e; float f; split(x, e, f); return e; }
     __device__ static __forceinline__ float ldexp_rn(float f, int e)
     {
-        if (f == 0.0f) return f;
+        if (eq0(f)) return f;
         uint32_t b = fbits(f), keep = b & (F_SIGN | F_MANT);
         if (e > 127) return ffrom((b & F_SIGN) | (0xFFu << 23));
         if (e >= -126) return ffrom(keep | ((uint32_t)(e + 127) << 23));
@@ -138,7 +140,7 @@ template <> struct fpt<float> {
     }
     __device__ static __forceinline__ float scale(float x, int s)
     {
-        if (x == 0.0f) return x;
+        if (eq0(x)) return x;
         int e; float f; split(x, e, f);
         return ldexp_rn(f, e + s);
     }
@@ -166,8 +168,11 @@ template <> struct fpt<float> {
 // (FP32: 1.1 times) slower on matrices of mixed zero pattern and wide exponent range
 // (measured on a GB300; the instruction stream grows with each copy, and divergent warps
 // fetch from all of them).  One shared body per function keeps the executed code small.
+// The out-of-line bodies take and return bit patterns (uint64_t): on sm_103 a call that
+// passes doubles spends FP64-pipe instructions on moving them (2 per call, measured), and
+// the FP64 pipe is the scarce one.
 // ---------------------------------------------------------------------------------------
-static __device__ __noinline__ double div_rn(double a, double b)
+__device__ __forceinline__ double div_rn_body(double a, double b)
 {
     const uint64_t ab = dbits(a), bb = dbits(b);
     const uint32_t Ea = (uint32_t)(ab >> 52) & 0x7FF, Eb = (uint32_t)(bb >> 52) & 0x7FF;
@@ -215,6 +220,9 @@ static __device__ __noinline__ double div_rn(double a, double b)
     if (rb && (st || (m & 1))) ++m;
     return dfrom(sign | m);                                 // m <= 2^52: subnormal or 2^-1022
 }
+
+static __device__ __noinline__ uint64_t div_rn_bits(uint64_t a, uint64_t b) { return dbits(div_rn_body(dfrom(a), dfrom(b))); }
+__device__ __forceinline__ double div_rn(double a, double b) { return dfrom(div_rn_bits(dbits(a), dbits(b))); }
 
 // the method's divisions: binary64 on the integer pipes, binary32 on the FP32 pipe
 __device__ __forceinline__ double qdiv(double a, double b) { return div_rn(a, b); }
@@ -300,7 +308,7 @@ template <typename T> __device__ __forceinline__ ef<T> ef_minus(T x, T y)
     int c = fpt<T>::EMU + fpt<T>::P - 1 - (ex < ey ? ex : ey);
     z = fpt<T>::scale(x, c) - fpt<T>::scale(y, c);
     w = ef_of(z);
-    if (w.f != T(0)) w.e -= c;
+    if (!eq0(w.f)) w.e -= c;
     return w;
 }
 
@@ -308,23 +316,26 @@ template <typename T> __device__ __forceinline__ ef<T> ef_minus(T x, T y)
 // floor(sqrt(X)) for an integer X in [2^110, 2^113), and the remainder X - floor(sqrt(X))^2,
 // on the integer pipes (Newton's method for the square root):
 //   * s0 = sqrt(X) (1 + e), |e| < 2^-21.4, from the FP32 reciprocal square root y of the
-//     leading 31 bits of X (rsqrtf is within 2 ulp);
-//   * two corrections s <- s + (X - s^2) / (2 s): the residual is exact in 128-bit
-//     integers, the quotient R y / 2 is formed in FP32 from its leading bits and rounded to
-//     an integer.  Each error bound: |s1 - sqrt X| < 2^14.2 (Newton's quadratic term
-//     e0^2 / 2 s0) + 2^14.8 (the FP32 quotient, 2^-20.3 relative of |e0| < 2^35.1) + 1/2,
-//     then |s2 - sqrt X| < 1/2 + 2^-4.7;
+//     leading 31 bits of X (rsqrtf is within 2 ulp); Y = y 2^45 ~ 2^86 / sqrt(X) as a
+//     32-bit integer;
+//   * two corrections s <- s + (X - s^2) / (2 s) ~ s + R Y 2^-87: the residual R is exact
+//     in 128-bit integers, its leading 31 bits times Y is one 32x32->64-bit product.  Error
+//     bounds: |s1 - sqrt X| < 2^14.2 (Newton's quadratic term e0^2 / 2 sqrt X) + 2^13.5
+//     (Y's relative error times |R0| / 2 sqrt X < 2^35.1) + 2^6 (R0 truncated to 31 bits) +
+//     1 < 2^14.9, then |s2 - sqrt X| < 1/2 + 2^-6.7 + 2^-13;
 //   * floor(sqrt X) is s2 or s2 - 1, decided by the sign of X - s2^2.
+// No conversion involves a 64-bit type (those run on the FP64 pipe).
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t isqrt113(u128 X, u128 &rem)
 {
     const float xf = __uint2float_rz((uint32_t)(X >> 82));           // [2^28, 2^31)
-    const float y = rsqrtf(xf);                                       // 2^41 / sqrt(X), within 2^-21.6
-    uint64_t s = (uint64_t)__float2ull_rn(xf * y * 0x1p41f);
-    __int128 R = (__int128)(X - (u128)s * s);                         // |R| < 2^93
-    s += (uint64_t)__float2ll_rn(__ll2float_rn((long long)(R >> 40)) * y * 0x1p-2f);
-    R = (__int128)(X - (u128)s * s);                                  // |R| < 2^73.2
-    s += (uint64_t)__float2ll_rn(__ll2float_rn((long long)(R >> 16)) * y * 0x1p-26f);
+    const float y = rsqrtf(xf);                                       // 2^41 / sqrt(X)
+    const int64_t Y = (int64_t)__float2uint_rn(y * 0x1p45f);          // (2^29.5, 2^31]
+    uint64_t s = (uint64_t)__float2uint_rn(xf * y * 0x1p9f) << 32;
+    __int128 R = (__int128)(X - (u128)s * s);                         // |R| < 2^92.6
+    s += (uint64_t)(((int64_t)(int32_t)(int64_t)(R >> 62) * Y) >> 25);
+    R = (__int128)(X - (u128)s * s);                                  // |R| < 2^72.5
+    s += (uint64_t)(((int64_t)(int32_t)(int64_t)(R >> 43) * Y + (1ll << 43)) >> 44);
     R = (__int128)(X - (u128)s * s);
     if (R < 0) { R += (__int128)(2 * s) - 1; s -= 1; }
     rem = (u128)R;
@@ -342,11 +353,12 @@ __device__ __forceinline__ uint64_t isqrt113(u128 X, u128 &rem)
 //    candidate sqrt(fma(a', a', b'*b')) is corrected by comparing the exact a'^2 + b'^2 with
 //    the squared midpoints to the neighbouring values, in integers (units 2^-52).
 // ---------------------------------------------------------------------------------------
-static __device__ __noinline__ double hypot_cr(double x, double y)
+__device__ __forceinline__ double hypot_cr_body(double x, double y)
 {
     uint64_t ab = dbits(x) & ~D_SIGN, bb = dbits(y) & ~D_SIGN;
     if (ab < bb) { uint64_t t = ab; ab = bb; bb = t; }
-    if ((ab >> 52) == 0x7FF) return dfrom(ab) + dfrom(bb);    // inf or nan
+    if ((ab >> 52) == 0x7FF)                                 // inf, or a quiet nan
+        return dfrom((ab << 12) ? (ab | 0x0008000000000000ull) : ab);
     if (bb == 0) return dfrom(ab);
     const int Ea = (int)(ab >> 52), Eb = (int)(bb >> 52);
     uint64_t A = ab & D_MANT, B = bb & D_MANT;
@@ -387,6 +399,9 @@ static __device__ __noinline__ double hypot_cr(double x, double y)
     if (E >= 2047) return dfrom(0x7FFull << 52);
     return dfrom(((uint64_t)E << 52) | (R & D_MANT));
 }
+
+static __device__ __noinline__ uint64_t hypot_cr_bits(uint64_t x, uint64_t y) { return dbits(hypot_cr_body(dfrom(x), dfrom(y))); }
+__device__ __forceinline__ double hypot_cr(double x, double y) { return dfrom(hypot_cr_bits(dbits(x), dbits(y))); }
 
 static __device__ __noinline__ float hypot_cr(float x, float y)
 {
@@ -482,7 +497,7 @@ __device__ __forceinline__ void round113(u128 m, int e, bool sticky, u128 &M, in
     }
 }
 
-static __device__ __noinline__ double ext_num_div(double x1, double y1, double x2, double y2, bool sub, double d)
+__device__ __forceinline__ double ext_num_div_body(double x1, double y1, double x2, double y2, bool sub, double d)
 {
     uint64_t a1, b1, a2, b2; int ea1, eb1, ea2, eb2; bool na1, nb1, na2, nb2;
     dmant(x1, a1, ea1, na1); dmant(y1, b1, eb1, nb1);
@@ -515,7 +530,7 @@ static __device__ __noinline__ double ext_num_div(double x1, double y1, double x
     dmant(d, Md, ed, nd);
     uint64_t r = (uint64_t)(M1 >> 61);                      // top 52 bits of M1, below Md
     u128 rest = (M1 & ((((u128)1) << 61) - 1)) << 56;      // the remaining 117 bits
-    const float mhi = __ull2float_rn(Md >> 29);             // exact, in [2^23, 2^24)
+    const float mhi = __uint2float_rn((uint32_t)(Md >> 29));  // exact, in [2^23, 2^24)
     u128 q = 0;
     int left = 117;
 #pragma unroll 1
@@ -523,9 +538,9 @@ static __device__ __noinline__ double ext_num_div(double x1, double y1, double x
         int w = left >= 20 ? 20 : left;
         left -= w;
         u128 rp = ((u128)r << w) | ((rest >> left) & ((((u128)1) << w) - 1));
-        float rhi = __ull2float_rn((uint64_t)(rp >> 49));    // exact: rp < 2^73
+        float rhi = __uint2float_rn((uint32_t)(rp >> 49));   // exact: rp < 2^73
         float qf = __fmul_rn(__fdiv_rn(rhi, mhi), 1048576.0f);
-        uint64_t qd = (uint64_t)qf;
+        uint64_t qd = __float2uint_rz(qf);           // qf <= 2^21
         if (qd > (1ull << w)) qd = 1ull << w;
         u128 prod = (u128)qd * Md;
 #pragma unroll 1
@@ -567,6 +582,14 @@ static __device__ __noinline__ double ext_num_div(double x1, double y1, double x
         bits = Mr;                                          // subnormal (or 2^-1022 after a carry)
     }
     return dfrom(bits | (neg ? D_SIGN : 0));
+}
+static __device__ __noinline__ uint64_t ext_num_div_bits(uint64_t x1, uint64_t y1, uint64_t x2, uint64_t y2, bool sub, uint64_t d)
+{
+    return dbits(ext_num_div_body(dfrom(x1), dfrom(y1), dfrom(x2), dfrom(y2), sub, dfrom(d)));
+}
+__device__ __forceinline__ double ext_num_div(double x1, double y1, double x2, double y2, bool sub, double d)
+{
+    return dfrom(ext_num_div_bits(dbits(x1), dbits(y1), dbits(x2), dbits(y2), sub, dbits(d)));
 }
 
 // eq. (EXT) for float: the wide type is double, where the products of floats are exact

@@ -110,7 +110,7 @@ __device__ __forceinline__ void simple9(int tt, T g11, T g21, T g12, T g22, m22<
     if (lt0(b)) neg_col(U, 1);
     V = ident<T>();
     if (pv) swap_rows(V);
-    d1 = fabs(a); d2 = fabs(b);
+    d1 = absv(a); d2 = absv(b);
 }
 
 // Sect. 3.1, classes 3 (one non-zero column) and 5 (one non-zero row): one Givens rotation
@@ -123,7 +123,7 @@ __device__ __forceinline__ void simple35(int tt, T g11, T g21, T g12, T g22, m22
     if (col) { p0 = (tt == 12); x0 = p0 ? g12 : g11; x1 = p0 ? g22 : g21; }
     else { p0 = (tt == 10); x0 = p0 ? g21 : g11; x1 = p0 ? g22 : g12; }
     bool n0 = lt0(x0), n1 = lt0(x1);
-    T y0 = fabs(x0), y1 = fabs(x1);
+    T y0 = absv(x0), y1 = absv(x1);
     bool p1 = pos_lt(y0, y1);
     T x = p1 ? y1 : y0, y = p1 ? y0 : y1;
     T c, s;
@@ -258,9 +258,9 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
         else if (tp == 11) { a = g22; b = g21; d = g11; }
         else if (tp == 14) { a = g21; b = g22; d = g12; }
         else { a = g11; b = g12; d = g22; }
-        bool n11 = lt0(a); a = fabs(a); if (n11) b = ngt(b);
-        bool n12 = lt0(b); b = fabs(b); if (n12) d = ngt(d);
-        bool n22 = lt0(d); d = fabs(d);
+        bool n11 = lt0(a); a = absv(a); if (n11) b = ngt(b);
+        bool n12 = lt0(b); b = absv(b); if (n12) d = ngt(d);
+        bool n22 = lt0(d); d = absv(d);
         tri_out<T> z;
         tri_svd(a, b, d, z, flags);
         m22<T> U = ucheck(z);                              // U = P_U S11 S22 U-check
