@@ -204,3 +204,65 @@ def test_config4_sampled_and_forms_agree():
     plain = _gpu(flat[:end], sl, 1)
     _same(plain, tuple(x[:end] if k in (0, 2) else (x[:int(soffs[512])] if k == 1 else x[:512])
                        for k, x in enumerate(got)), "plain vs persistent")
+
+
+def test_config5_gradients():
+    """Batched Kogbetliantz with gradients: 2048 FP64 matrices of order uniform in {32..256}
+    and 4096 FP32 matrices of order uniform in {8..128} (built as the batched workload),
+    sigma backpropagated to A (dA = U diag(dsigma) V^T) through the autograd function with
+    the tuned block sizes.  Sampled matrices match the oracle bit for bit (U, S, V and the
+    gradient); central differences on 64 FP64 matrices, all perturbed at once (the matrices
+    are independent), agree with the gradient."""
+    from paper_2407_13116_gb300.autograd import kogbet_sigma
+    seed = 0x240713116 + 5
+    for prec, count, lo, hi in (("d", 2048, 32, 256), ("s", 4096, 8, 128)):
+        T = np.float64 if prec == "d" else np.float32
+        orders = I.kog_orders(count, lo, hi, seed + (prec == "s"))
+        flat, sig = I.kog_batch(orders, seed + (prec == "s"), dtype=T)
+        A = torch.from_numpy(flat).to(DEV).requires_grad_(True)
+        U, S, V, sw, info = kogbet_sigma(A, list(orders))
+        assert bool((info == 0).all())
+        w = torch.from_numpy(np.cos(np.arange(S.numel()) * 0.37).astype(T)).to(DEV)
+        (g,) = torch.autograd.grad((S * w).sum(), A, retain_graph=True)
+        Un, Sn, Vn, gn, wn = (x.detach().cpu().numpy() for x in (U, S, V, g, w))
+        offs = np.concatenate([[0], np.cumsum(orders.astype(np.int64) ** 2)[:-1]])
+        soffs = np.concatenate([[0], np.cumsum(orders.astype(np.int64))[:-1]])
+        pick = [int(np.argmax(orders)), int(np.argmin(orders))] + list(np.random.default_rng(5).integers(0, count, 3))
+        for i in pick:
+            n = int(orders[i])
+            a = flat[offs[i]:offs[i] + n * n].reshape(n, n).T
+            u, s, v, _, _ = oracle.kogbet(a, prec)
+            assert np.array_equal(_bits(Sn[soffs[i]:soffs[i] + n]), _bits(s))
+            assert np.array_equal(_bits(Un[offs[i]:offs[i] + n * n]), _bits(u.T.reshape(-1)))
+            assert np.array_equal(_bits(Vn[offs[i]:offs[i] + n * n]), _bits(v.T.reshape(-1)))
+            ref = oracle.kog_sigma_bwd(u, v, wn[soffs[i]:soffs[i] + n], prec)
+            assert np.array_equal(_bits(gn[offs[i]:offs[i] + n * n]), _bits(ref.T.reshape(-1)))
+        if prec != "d":
+            continue
+        # central differences: loss sum_k c_k sigma_k over the four largest singular values of
+        # each of 64 matrices whose top five are separated by more than 1e-2 relative
+        h = 1e-6
+        cand = [i for i in range(count) if np.all(-np.diff(sig[i][:5]) > 1e-2 * sig[i][0])][:64]
+        assert len(cand) == 64
+        sel = [int(i) for i in cand]
+        so = [list(range(int(soffs[i]), int(soffs[i]) + 4)) for i in sel]
+        c = np.array([1.0, -0.7, 0.4, 0.25])
+        dAp, dAm = flat.copy(), flat.copy()
+        rng = np.random.default_rng(9)
+        pos = []
+        for i in sel:
+            n = int(orders[i])
+            e = int(offs[i]) + int(rng.integers(0, n * n))
+            pos.append(e)
+            dAp[e] += h
+            dAm[e] -= h
+        Sp = k2().kogbet(torch.from_numpy(dAp).to(DEV), list(orders))[1].cpu().numpy()
+        Sm = k2().kogbet(torch.from_numpy(dAm).to(DEV), list(orders))[1].cpu().numpy()
+        wt = torch.zeros_like(S)
+        for idx in so:
+            wt[idx] = torch.from_numpy(c).to(DEV)
+        (g4,) = torch.autograd.grad((S * wt).sum(), A)
+        g4 = g4.cpu().numpy()
+        for i, e, idx in zip(sel, pos, so):
+            fd = float(((Sp[idx] - Sm[idx]) * c).sum()) / (2 * h)
+            assert abs(fd - g4[e]) <= 1e-6 * max(1.0, abs(g4[e])), (i, e, fd, g4[e])
