@@ -166,6 +166,22 @@ def fp64_peak(clock_mhz):
     return sms * 2.0 * clock_mhz * 1e6
 
 
+def hbm_peak_gbs():
+    """The measured HBM copy bandwidth of this GPU model (MEASURED_PEAKS.json), else the
+    earlier measurement on a GB300 (6.8 TB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+# FP64 operations of the 2x2 adjoint per matrix (k2svd_dgesvd2_bwd): J12 - J21 and K12 - K21
+# (2 fma, 2 mul, 1 add each), the gap and F12 (2 add, 2 mul, 1 division), the two
+# off-diagonal entries of M (fma, mul, mul each), W = U M and dG = W V^T (8 each).
+BWD_OPS = {"arith": 36, "div": 1}
+
+
 def load_opcounts():
     with open(os.path.join(ROOT, "tests", "golden", "opcounts.json")) as f:
         return json.load(f)["workloads"]
@@ -254,7 +270,7 @@ def leg(prec, n_half, steps, warmup, dev, D, clocks_index=None):
     return {"ms": ms, "ge_ms": ge_ms, "tr_ms": tr_ms, "clocks": clocks, "launches": 2 * steps}
 
 
-def fwd_bwd_leg(steps, warmup, dev, D):
+def fwd_bwd_leg(steps, warmup, dev, D, rates, clk_mhz):
     """The differentiation workload: 2^24 FP64 matrices R(theta) diag(s1, s2) R(phi)^T; one step
     is the forward (k2svd_dgesvd2) and the backward (k2svd_dgesvd2_bwd) with upstream
     gradients dS, dU, dV ~ N(0,1)."""
@@ -296,11 +312,21 @@ def fwd_bwd_leg(steps, warmup, dev, D):
     bwd_bytes = 192 * n
     del G, dS, dU, dV, U, V, S, dG
     torch.cuda.empty_cache()
+    hbm, hbm_src = hbm_peak_gbs()
+    ops = BWD_OPS["arith"] + BWD_OPS["div"] * rates["dfma"] / rates["ddiv"]
+    peak = fp64_peak(clk_mhz)
+    t_fp64, t_hbm = n * ops / peak, bwd_bytes / (hbm * 1e9)
     return {"value": D.world * n / (ms / 1e3), "unit": "fwd+bwd/s", "matrices_per_gpu_per_step": n,
             "fwd_ms": fwd, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd,
-            "bwd_roofline": {"bound": "hbm", "achieved": bwd_bytes / (bwd / 1e3) / 1e9, "peak": 6691.5,
-                             "unit": "GB/s", "frac": bwd_bytes / (bwd / 1e3) / 6691.5e9,
-                             "algorithmic_bytes": bwd_bytes},
+            "bwd_roofline": {"bound": "alu" if t_fp64 > t_hbm else "hbm",
+                             "achieved": n * ops / (bwd / 1e3) / 1e9, "peak": peak / 1e9,
+                             "unit": "G FP64-pipe op/s", "frac": (n * ops / (bwd / 1e3)) / peak,
+                             "ops_per_matrix": ops, "algorithmic_bytes": bwd_bytes,
+                             "hbm_frac": bwd_bytes / (bwd / 1e3) / (hbm * 1e9), "hbm_peak_gbs": hbm,
+                             "hbm_peak_source": hbm_src,
+                             "note": "the lesser of HBM (192 B/matrix) and the FP64 pipe over the adjoint's "
+                                     "operations, the division at its FP64-pipe cost; the kernel divides on "
+                                     "the integer pipes"},
             "workload": "2^24 FP64 R(theta) diag(s1,s2) R(phi)^T, 10% near-equal singular values, upstream N(0,1)"}
 
 
@@ -473,7 +499,10 @@ def run_ours(a):
                                "live probe reached %.3g DFMA/s; divide %.2f, sqrt %.2f fma slots (probe)" % (
                                    clk_mhz, rates["dfma"], rates["dfma"] / rates["ddiv"], rates["dfma"] / rates["dsqrt"]),
                 "step_frac": value / D.world / roof_step,
-                "hbm_bound_svds_per_s": 1e9 * 6691.5 / ((BYTES_GE["d"] + BYTES_TR["d"]) / 2)}
+                "note": "roofline of the method's counted operations (oracle counters) at their FP64-pipe issue "
+                        "cost, divisions and square roots weighted by the probe; the kernel runs the divisions, "
+                        "the hypot, comparisons and exact steps on the integer pipes, so it may pass this bound",
+                "hbm_bound_svds_per_s": 1e9 * hbm_peak_gbs()[0] / ((BYTES_GE["d"] + BYTES_TR["d"]) / 2)}
     out = {"metric": METRIC, "value": value, "unit": "SVDs/s", "n_gpus": D.world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -491,14 +520,14 @@ def run_ours(a):
         cs_tr = slot_costs(oc["wide_s_trsvd2"], rates, "s")
         roof32 = 2 / ((cs_ge["fp32"] + cs_tr["fp32"]) / rates["ffma"])
         roof64 = 2 / ((cs_ge["fp64"] + cs_tr["fp64"]) / rates["dfma"])
-        roofhbm = 2 / ((BYTES_GE["s"] + BYTES_TR["s"]) / 6691.5e9)
+        roofhbm = 2 / ((BYTES_GE["s"] + BYTES_TR["s"]) / (hbm_peak_gbs()[0] * 1e9))
         vs = D.world * 2 * N_HALF_S / (mss / 1e3)
         out["fp32"] = {"value": vs, "unit": "SVDs/s", "ms_per_step": mss, "matrices_per_gpu_per_step": 2 * N_HALF_S,
                        "roofline_svds_per_s": {"fp32_pipe": roof32, "fp64_pipe": roof64, "hbm": roofhbm},
                        "frac_of_min_roofline": vs / D.world / min(roof32, roof64, roofhbm),
                        "gesvd2_ms": rs["ge_ms"], "trsvd2_ms": rs["tr_ms"]}
     if not a.no_fwd_bwd:
-        out["fwd_bwd"] = fwd_bwd_leg(a.steps, a.warmup, dev, D)
+        out["fwd_bwd"] = fwd_bwd_leg(a.steps, a.warmup, dev, D, rates, clk_mhz)
     if not a.no_kog:
         out["kogbet"] = kog_leg(max(2, a.steps // 3), 1, dev, D)
     if D.world == 1 and not a.no_e2e:

@@ -37,15 +37,18 @@ __global__ void __launch_bounds__(256) bwd_kernel(const bwd_args<T> a)
             bm = fma(v11, e12, v21 * e22) - fma(v12, e11, v22 * e21);
         }
         T m12 = T(0), m21 = T(0);
-        if (!isfinite(s1) || !isfinite(s2)) {
+        // comparisons, the maximum and the division run on the integer pipes (the FP64
+        // pipe is the scarce one); the results are those of the IEEE operations
+        if (!is_fin(s1) || !is_fin(s2)) {
             m12 = m21 = T(NAN);
-        } else if (s1 > T(0)) {
+        } else if (gt0(s1)) {
             // scale by 2^-k with s1 2^-k in [1,2): F12 (a s2 + b s1) = -(a s2' + b s1') / (g' s') 2^-k
             int k; T f;
             fpt<T>::split(s1, k, f);
             const T s1n = f, s2n = fpt<T>::scale(s2, -k);
-            const T gap = fmax(s1n - s2n, a.tau * s1n);
-            const T q = T(1) / (gap * (s1n + s2n));
+            const T d = s1n - s2n, t = a.tau * s1n;              // both >= 0
+            const T gap = pos_lt(d, t) ? t : d;
+            const T q = qdiv(T(1), gap * (s1n + s2n));
             m12 = fpt<T>::scale(-fma(am, s2n, bm * s1n) * q, -k);
             m21 = fpt<T>::scale(-fma(am, s1n, bm * s2n) * q, -k);
         }

@@ -39,6 +39,8 @@ __device__ __forceinline__ int clz128(u128 x)
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ bool lt0(double x) { int64_t b = (int64_t)dbits(x); return b < 0 && (b << 1) != 0; }
 __device__ __forceinline__ bool lt0(float x) { int32_t b = (int32_t)fbits(x); return b < 0 && (b << 1) != 0; }
+__device__ __forceinline__ bool gt0(double x) { return (int64_t)dbits(x) > 0; }
+__device__ __forceinline__ bool gt0(float x) { return (int32_t)fbits(x) > 0; }
 __device__ __forceinline__ bool eq0(double x) { return (dbits(x) << 1) == 0; }
 __device__ __forceinline__ bool eq0(float x) { return (fbits(x) << 1) == 0; }
 __device__ __forceinline__ bool pos_lt(double a, double b) { return dbits(a) < dbits(b); }
