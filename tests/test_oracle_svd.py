@@ -280,3 +280,33 @@ def test_single_precision_accuracy():
     T = I.triangular(1024, 83, "s", "wide")
     a = oracle.trsvd2(T[0], T[1], T[2], "s")
     assert np.isfinite(a["U"]).all() and np.isfinite(a["V"]).all()
+
+
+def test_operation_counts_by_hand():
+    """The oracle's operation counters against counts read off the formulas, one input per
+    class.  These counts feed the roofline (tests/golden/opcounts.json).
+    * diagonal (t = 9): a signed permutation, no arithmetic;
+    * one nonzero column or row (t = 3, 5; Sect. 3.1): tan = small/big, sigma1 = hypot,
+      sec = hypot(tan, 1), cos = 1/sec, sin = tan/sec: 3 div, 2 hypot;
+    * upper triangular, general Alg. 1 branch (t' = 13): h = hypot(r11, r12), the test
+      r11/r12 < eps, h (+) r22 and h (-) r22, 2 (.) r12 (.) r22 and d (.) s, their quotient;
+      tan phi = t2/(1 + hypot(t2, 1)), sec, cos and sin of phi; Alg. 2: t = fma(r22, tan phi,
+      r12), tan psi = t/r11, sec, cos and sin of psi, sec phi (/) sec psi, r11 (/) it and
+      r22 (.) it: 3 add, 3 mul, 1 fma, 10 div, 4 hypot;
+    * no zeros (t' = 15, Sect. 3.2.2) with an inexact tan theta: two column hypots,
+      tan theta and sec theta, the exactness fma, one element by fma and division, the
+      other by (EXT) and division; the triangular SVD as above; the heuristic's
+      tan phi +- tan theta, its fma denominator, the quotient and its sec, cos and sin:
+      4 add, 3 mul, 4 fma, 16 div, 8 hypot, 1 (EXT)."""
+    def count(g, tri=False):
+        if tri:
+            return oracle.opcount(np.array(g, dtype=np.float64).reshape(3, 1), triangular=True)
+        return oracle.opcount(np.array(g, dtype=np.float64).reshape(4, 1))
+    z = dict(add=0, mul=0, fma=0, div=0, hypot=0, ext=0)
+    assert count([2.0, 0.0, 0.0, 3.0]) == z
+    assert count([2.0, 3.0, 0.0, 0.0]) == dict(z, div=3, hypot=2)
+    assert count([2.0, 0.0, 3.0, 0.0]) == dict(z, div=3, hypot=2)
+    tri = dict(add=3, mul=3, fma=1, div=10, hypot=4, ext=0)
+    assert count([2.0, 0.0, 1.0, 3.0]) == tri
+    assert count([2.0, 1.0, 3.0], tri=True) == tri
+    assert count([2.0, 1.0, 0.5, 3.0]) == dict(add=4, mul=3, fma=4, div=16, hypot=8, ext=1)
