@@ -30,7 +30,7 @@ N_HALF_S = 1 << 28
 E2E_HALF = 1 << 25
 N_DIFF = 1 << 24
 N_KOG = 8192
-E2E_CHUNK = 1 << 22
+E2E_CHUNK = 1 << 21
 METRIC = "FP64 2×2 SVDs/s & % of roofline; fwd+bwd/s; batched Kogbetliantz speedup"
 BYTES_GE = {"d": 112, "s": 56}          # in 4 T + out (4 U + 4 V + 2 S) T
 BYTES_TR = {"d": 104, "s": 52}          # in 3 T + out 10 T
@@ -388,13 +388,16 @@ def kog_leg(steps, warmup, dev, D):
 
 def e2e_leg(steps, warmup, dev):
     """End to end through the Python API: pinned host inputs -> device -> kernels -> host
-    outputs, in chunks over two streams so that copies overlap the kernels."""
+    outputs, in chunks over three streams with a buffer set each, so that the host-to-device
+    copy of one chunk, the kernel of another and the device-to-host copy of a third run at
+    the same time (ordering only within a stream; all streams join at the end of a step)."""
     import torch
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
     n, c = E2E_HALF, E2E_CHUNK
     nc = n // c
     dt = torch.float64
+    NS = 3
 
     def chunked(x):       # (k, n) -> (nc, k, c): every chunk one contiguous block
         return x.reshape(x.shape[0], nc, c).permute(1, 0, 2).contiguous()
@@ -403,21 +406,22 @@ def e2e_leg(steps, warmup, dev):
     Th = chunked(I.triangular(n, SEED + 3, "d", "wide", xp="torch", device=dev)).cpu().pin_memory()
     outs = {k: torch.empty((nc, rows, c), dtype=dt, pin_memory=True) for k, rows in
             (("Ug", 4), ("Vg", 4), ("Sg", 2), ("Ut", 4), ("Vt", 4), ("St", 2))}
-    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
     bufs = []
-    for _ in range(2):
+    for _ in range(NS):
         bufs.append({"G": torch.empty((4, c), dtype=dt, device=dev), "T": torch.empty((3, c), dtype=dt, device=dev),
                      "U": torch.empty((4, c), dtype=dt, device=dev), "V": torch.empty((4, c), dtype=dt, device=dev),
                      "S": torch.empty((2, c), dtype=dt, device=dev)})
     main = torch.cuda.current_stream()
 
     def step():
+        for st in streams:
+            st.wait_stream(main)
         j = 0
         for kind in ("g", "t"):
             for q in range(nc):
-                st, b = streams[j % 2], bufs[j % 2]
+                st, b = streams[j % NS], bufs[j % NS]
                 j += 1
-                st.wait_stream(main)
                 with torch.cuda.stream(st):
                     if kind == "g":
                         b["G"].copy_(Gh[q], non_blocking=True)
@@ -430,7 +434,8 @@ def e2e_leg(steps, warmup, dev):
                     U[q].copy_(b["U"], non_blocking=True)
                     V[q].copy_(b["V"], non_blocking=True)
                     S[q].copy_(b["S"], non_blocking=True)
-                main.wait_stream(st)
+        for st in streams:
+            main.wait_stream(st)
         torch.cuda.synchronize()
 
     for _ in range(warmup):
@@ -442,7 +447,7 @@ def e2e_leg(steps, warmup, dev):
     h2d = (4 + 3) * 8 * n
     d2h = 2 * (4 + 4 + 2) * 8 * n
     return {"value": 2 * n / el, "unit": "SVDs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "batch": 2 * n, "ms_per_step": el * 1e3}
+            "batch": 2 * n, "ms_per_step": el * 1e3, "streams": NS, "chunk": c}
 
 
 def cpu_baseline(seconds=10.0):
