@@ -67,6 +67,8 @@ def lib():
                 fn = getattr(L, "k2ref_hypot_" + sfx)
                 fn.argtypes = [T, T]
                 getattr(L, "k2ref_hypot_n_" + sfx).argtypes = [I64, P, P, P, C.c_int]
+                getattr(L, "k2ref_prescale2_" + sfx).argtypes = [I64, P, I64, P, I64, P, P, I32, C.c_int]
+                getattr(L, "k2ref_lasv2_" + sfx).argtypes = [I64, P, P, P, P, P, P, P, P, P, C.c_int]
                 fn.restype = T
                 getattr(L, "k2ref_trace_" + sfx).argtypes = [P, P, P]
                 getattr(L, "k2ref_efops_" + sfx).argtypes = [T, T, P, P]
@@ -152,6 +154,34 @@ def hypot_n(x, y, prec="d", nthreads=1):
     h = np.empty_like(x)
     getattr(lib(), "k2ref_hypot_n_" + prec)(x.size, _ptr(x), _ptr(y), _ptr(h), int(nthreads))
     return h
+
+
+def prescale2(G, prec="d", extra=0, nthreads=1):
+    """Phase 1 alone (Sect. 3.1): (Gs, s, types) for SoA planes G[4, n]: Gs = 2^s G with the
+    scale type raised by `extra`, types = t | t' << 4 (-1 for non-finite input)."""
+    T = _dt(prec)
+    G = np.ascontiguousarray(G, dtype=T)
+    n = G.shape[1]
+    Gs = np.empty_like(G); s = np.empty(n, np.int32); types = np.empty(n, np.int32)
+    rc = getattr(lib(), "k2ref_prescale2_" + prec)(n, _ptr(G), n, _ptr(Gs), n, _ptr(s), _ptr(types), int(extra),
+                                                    int(nthreads))
+    if rc != 0:
+        raise ValueError("k2ref_prescale2 returned %d" % rc)
+    return Gs, s, types
+
+
+def lasv2(F, Gp, H, prec="d", nthreads=1):
+    """The xLASV2 argument shape by the method: (ssmin, ssmax, snr, csr, snl, csl) with
+    [csl snl; -snl csl] [[F, Gp], [0, H]] [csr -snr; snr csr] = diag(ssmax, ssmin)."""
+    T = _dt(prec)
+    F = np.ascontiguousarray(F, dtype=T); Gp = np.ascontiguousarray(Gp, dtype=T)
+    H = np.ascontiguousarray(H, dtype=T)
+    n = F.shape[0]
+    out = [np.empty(n, T) for _ in range(6)]
+    rc = getattr(lib(), "k2ref_lasv2_" + prec)(n, _ptr(F), _ptr(Gp), _ptr(H), *[_ptr(o) for o in out], int(nthreads))
+    if rc != 0:
+        raise ValueError("k2ref_lasv2 returned %d" % rc)
+    return tuple(out)
 
 
 def trace(g, prec="d"):
