@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-fp32", action="store_true")
     p.add_argument("--no-fwd-bwd", action="store_true")
     p.add_argument("--no-kog", action="store_true")
+    p.add_argument("--no-phases", action="store_true")
     p.add_argument("--profile-case", choices=["d", "s", "kog"], default=None,
                    help="run a small case of the 2x2 kernels or of the persistent Kogbetliantz "
                         "kernel (for ncu captures) and exit")
@@ -386,6 +387,57 @@ def kog_leg(steps, warmup, dev, D):
                         "modulus strategy, off < n eps ||G||_F"}
 
 
+def phases_leg(steps, warmup, dev, D, rates, clk_mhz, oc):
+    """The standalone phase 1 (k2svd_dprescale2, extra = 1, on 2^27 general matrices) and the
+    xLASV2 argument shape (k2svd_dlasv2 on 2^27 triangular matrices) of the wide workload."""
+    import torch
+    from paper_2407_13116_gb300 import inputs as I
+    from paper_2407_13116_gb300 import k2svd
+    n = N_HALF_D
+    G = I.general(n, SEED + 2, "d", "wide", xp="torch", device=dev)
+    Gs = torch.empty_like(G)
+    res = {}
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        D.barrier()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return D.max(e0.elapsed_time(e1) / steps)
+
+    ms = timed(lambda: k2svd.prescale2(G, extra=1, Gs=Gs))
+    hbm, hbm_src = hbm_peak_gbs()
+    nbytes = 72 * n
+    res["prescale2"] = {"value": D.world * n / (ms / 1e3), "unit": "matrices/s", "ms": ms,
+                        "roofline": {"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm,
+                                     "unit": "GB/s", "frac": nbytes / (ms / 1e3) / (hbm * 1e9),
+                                     "algorithmic_bytes": nbytes, "peak_source": hbm_src},
+                        "workload": "2^27 wide-range FP64 general matrices, extra = 1 (G in 32 B, Gs out 32 B, s, types)"}
+    del G, Gs
+    T3 = I.triangular(n, SEED + 3, "d", "wide", xp="torch", device=dev)
+    outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(6)]
+    L = k2svd.lib()
+    ptrs = [o.data_ptr() for o in outs]
+    st = torch.cuda.current_stream().cuda_stream
+    ms = timed(lambda: L.k2svd_dlasv2(n, T3[0].data_ptr(), T3[1].data_ptr(), T3[2].data_ptr(), *ptrs, st))
+    cost = slot_costs(oc["wide_d_trsvd2"], rates, "d")["fp64"]
+    peak = fp64_peak(clk_mhz)
+    res["lasv2"] = {"value": D.world * n / (ms / 1e3), "unit": "SVDs/s", "ms": ms,
+                    "roofline": {"bound": "alu", "achieved": n * cost / (ms / 1e3) / 1e9, "peak": peak / 1e9,
+                                 "unit": "G FP64-pipe op/s", "frac": n * cost / (ms / 1e3) / peak,
+                                 "ops_per_matrix": cost, "algorithmic_bytes": 72 * n},
+                    "workload": "2^27 wide-range FP64 upper-triangular matrices (F, G, H in, 6 planes out)"}
+    del T3, outs
+    torch.cuda.empty_cache()
+    return res
+
+
 def e2e_leg(steps, warmup, dev):
     """End to end through the Python API: pinned host inputs -> device -> kernels -> host
     outputs, in chunks over three streams with a buffer set each, so that the host-to-device
@@ -533,6 +585,8 @@ def run_ours(a):
                        "gesvd2_ms": rs["ge_ms"], "trsvd2_ms": rs["tr_ms"]}
     if not a.no_fwd_bwd:
         out["fwd_bwd"] = fwd_bwd_leg(a.steps, a.warmup, dev, D, rates, clk_mhz)
+    if not a.no_phases:
+        out["phases"] = phases_leg(a.steps, a.warmup, dev, D, rates, clk_mhz, oc)
     if not a.no_kog:
         out["kogbet"] = kog_leg(max(2, a.steps // 3), 1, dev, D)
     if D.world == 1 and not a.no_e2e:

@@ -100,6 +100,49 @@ int k2svd_strsvd2(int64_t batch, const float *F, const float *Gu, const float *H
                   int32_t *info, void *stream);
 
 /*
+ * k2svd_dprescale2 / k2svd_sprescale2 -- phase 1 of the method on its own (Sect. 3.1,
+ * eqs. (eG), (s); the phases "can be used on their own", Sect. 5): for each matrix the type
+ * t (bit k set when element k of (g11, g21, g12, g22) is nonzero), the exponent
+ * s = e_nu - e_G - (scale type + extra), where e_G is the largest exponent of a nonzero
+ * element and the scale type is 2 for matrices without zeros, else 1; matrices of class 9
+ * (at most one nonzero per row and column) are not scaled (s = 0).  Gs = 2^s G, exact for
+ * s >= 0 and one correct rounding per element otherwise; t' is the type of Gs.  extra = 1
+ * leaves the margin Sect. 4 suggests before calling xLASV2 on small inputs.
+ *
+ *   batch    number of matrices, >= 0
+ *   G, ldg   4-plane input (g11, g21, g12, g22), ldg >= batch
+ *   Gs, ldgs 4-plane output, ldgs >= batch; may be G with the same leading dimension
+ *   s        int32 plane: the exponent s of each matrix
+ *   types    nullable int32 plane: t | t' << 4, or -1 for a matrix with a non-finite element
+ *            (copied unchanged with s = 0)
+ *   extra    0 .. 64
+ * Argument order for error codes: 1 batch, 2 G, 3 ldg, 4 Gs, 5 ldgs, 6 s, 8 extra.
+ */
+int k2svd_dprescale2(int64_t batch, const double *G, int64_t ldg, double *Gs, int64_t ldgs, int32_t *s,
+                     int32_t *types, int32_t extra, void *stream);
+int k2svd_sprescale2(int64_t batch, const float *G, int64_t ldg, float *Gs, int64_t ldgs, int32_t *s,
+                     int32_t *types, int32_t extra, void *stream);
+
+/*
+ * k2svd_dlasv2 / k2svd_slasv2 -- the argument shape of LAPACK's xLASV2 (the SVD of an upper
+ * triangular 2x2 matrix, the case the paper compares against, Sects. 1 and 4), computed by
+ * this method: for R = [[F, G], [0, H]],
+ *     [ CSL  SNL ]  R  [ CSR  -SNR ]   =   [ SSMAX    0   ]
+ *     [-SNL  CSL ]     [ SNR   CSR ]       [   0    SSMIN ]
+ * with (CSL, SNL), (CSR, SNR) the first columns of the method's U and V (k2svd_?trsvd2),
+ * SSMAX = sigma1 >= 0 and SSMIN = +-sigma2 carrying the sign of det R.  Every output is a
+ * plane of `batch` elements (device pointers); a matrix with a non-finite input gets NaN
+ * outputs.  The values differ from LAPACK's (a different method; LAPACK may also return a
+ * negative SSMAX), the identity above holds for both.
+ * Argument order for error codes: 1 batch, 2 F, 3 G, 4 H, 5 ssmin, 6 ssmax, 7 snr, 8 csr,
+ * 9 snl, 10 csl.
+ */
+int k2svd_dlasv2(int64_t batch, const double *F, const double *G, const double *H, double *ssmin, double *ssmax,
+                 double *snr, double *csr, double *snl, double *csl, void *stream);
+int k2svd_slasv2(int64_t batch, const float *F, const float *G, const float *H, float *ssmin, float *ssmax,
+                 float *snr, float *csr, float *snl, float *csl, void *stream);
+
+/*
  * k2svd_dgesvd2_bwd / k2svd_sgesvd2_bwd -- adjoint (backward) of the batched 2x2 SVD.
  * The paper has no backward; this is the standard adjoint of a square SVD G = U S V^T
  * with distinct singular values, with a gap threshold for near-equal ones:

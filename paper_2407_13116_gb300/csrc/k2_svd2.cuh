@@ -224,23 +224,34 @@ template <typename T> __device__ __forceinline__ m22<T> vcheck(const tri_out<T> 
     return m;
 }
 
+// Phase 1 (Sect. 3.1, eqs. (eG), (s)): the type t of G, the prescaling exponent
+// s = e_nu - e_G - (scale type + extra) (class 9 is not scaled: s = 0), G <- 2^s G (exact
+// for s >= 0, one rounding per element otherwise), and the type t' of the scaled matrix.
+// extra = 0 in the method; the standalone entry allows more headroom.
 template <typename T>
-__device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
+__device__ __forceinline__ void phase1(T &g11, T &g21, T &g12, T &g22, int extra, int &t, int &s, int &tp)
 {
-    const int t = !eq0(g11) | (!eq0(g21) << 1) | (!eq0(g12) << 2) | (!eq0(g22) << 3);
+    t = !eq0(g11) | (!eq0(g21) << 1) | (!eq0(g12) << 2) | (!eq0(g22) << 3);
     const int cls = cls_of(t);
-    int s = 0, flags = 0;
-    if (cls != 9) {                                        // eqs. (eG), (s): class 9 is not scaled
+    s = 0;
+    if (cls != 9) {
         int eG = INT_MIN;
         if (!eq0(g11)) eG = max(eG, fpt<T>::expo(g11));
         if (!eq0(g21)) eG = max(eG, fpt<T>::expo(g21));
         if (!eq0(g12)) eG = max(eG, fpt<T>::expo(g12));
         if (!eq0(g22)) eG = max(eG, fpt<T>::expo(g22));
-        s = fpt<T>::ENU - eG - (cls == 15 ? 2 : 1);
+        s = fpt<T>::ENU - eG - (cls == 15 ? 2 : 1) - extra;
         g11 = fpt<T>::scale(g11, s); g21 = fpt<T>::scale(g21, s);
         g12 = fpt<T>::scale(g12, s); g22 = fpt<T>::scale(g22, s);
     }
-    const int tp = !eq0(g11) | (!eq0(g21) << 1) | (!eq0(g12) << 2) | (!eq0(g22) << 3);
+    tp = !eq0(g11) | (!eq0(g21) << 1) | (!eq0(g12) << 2) | (!eq0(g22) << 3);
+}
+
+template <typename T>
+__device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
+{
+    int t, s, tp, flags = 0;
+    phase1(g11, g21, g12, g22, 0, t, s, tp);
     const int clsp = cls_of(tp);
     bool simple = true;
     T d1 = T(0), d2 = T(0);

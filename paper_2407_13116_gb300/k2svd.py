@@ -49,6 +49,13 @@ def _bind_extra(L):
     L.k2svd_dgesvd2_bwd.restype = C.c_int
     L.k2svd_sgesvd2_bwd.argtypes = [I64, P, P, P, I64, P, P, P, P, F, P]
     L.k2svd_sgesvd2_bwd.restype = C.c_int
+    for p, T in (("d", D), ("s", F)):
+        f = getattr(L, "k2svd_%sprescale2" % p)
+        f.argtypes = [I64, P, I64, P, I64, P, P, I32, P]
+        f.restype = C.c_int
+        f = getattr(L, "k2svd_%slasv2" % p)
+        f.argtypes = [I64, P, P, P, P, P, P, P, P, P, P]
+        f.restype = C.c_int
     for p in ("d", "s"):
         f = getattr(L, "k2svd_%skogbet_ws" % p)
         f.argtypes = [I64, P, I32, C.POINTER(SZ)]
@@ -160,6 +167,46 @@ def trsvd2(F, Gu, H, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_e
     if rc != 0:
         raise K2SVDError("k2svd_%strsvd2 returned %d" % (p, rc))
     return U, V, S, Se, Sf, info
+
+
+def prescale2(G, extra=0, Gs=None, want_types=True):
+    """Phase 1 alone (k2svd_?prescale2): returns (Gs, s, types) with Gs = 2^s G (4, n) planes,
+    s the int32 exponents and types = t | t' << 4 (-1 for non-finite input)."""
+    p = _prefix(G.dtype)
+    dev = G.device
+    _check(G, "G", G.dtype, dev)
+    n = G.shape[1]
+    ldg = _planes(G, 4, "G")
+    Gs = torch.empty((4, n), dtype=G.dtype, device=dev) if Gs is None else Gs
+    _check(Gs, "Gs", G.dtype, dev)
+    ldgs = _planes(Gs, 4, "Gs")
+    s = torch.empty((n,), dtype=torch.int32, device=dev)
+    types = torch.empty((n,), dtype=torch.int32, device=dev) if want_types else None
+    with torch.cuda.device(dev):
+        rc = getattr(lib(), "k2svd_%sprescale2" % p)(n, _ptr(G), ldg, _ptr(Gs), ldgs, _ptr(s), _ptr(types),
+                                                     int(extra), _stream())
+    if rc != 0:
+        raise K2SVDError("k2svd_%sprescale2 returned %d" % (p, rc))
+    return Gs, s, types
+
+
+def lasv2(F, G, H):
+    """The xLASV2 argument shape by the method (k2svd_?lasv2): (ssmin, ssmax, snr, csr, snl,
+    csl), each (n,), with [csl snl; -snl csl] [[F, G], [0, H]] [csr -snr; snr csr] =
+    diag(ssmax, ssmin)."""
+    p = _prefix(F.dtype)
+    dev = F.device
+    for t, nm in ((F, "F"), (G, "G"), (H, "H")):
+        _check(t, nm, F.dtype, dev)
+        if t.dim() != 1 or (t.numel() > 1 and t.stride(0) != 1) or t.shape[0] != F.shape[0]:
+            raise K2SVDError("%s must be a contiguous vector of the length of F" % nm)
+    n = F.shape[0]
+    out = [torch.empty((n,), dtype=F.dtype, device=dev) for _ in range(6)]
+    with torch.cuda.device(dev):
+        rc = getattr(lib(), "k2svd_%slasv2" % p)(n, _ptr(F), _ptr(G), _ptr(H), *[_ptr(o) for o in out], _stream())
+    if rc != 0:
+        raise K2SVDError("k2svd_%slasv2 returned %d" % (p, rc))
+    return tuple(out)
 
 
 def gesvd2_bwd(U, S, V, dS=None, dU=None, dV=None, gap_rtol=1e-10, dG=None):
