@@ -32,6 +32,8 @@ int k2probe_rate(int op, double *rate);
  */
 int k2probe_div(int64_t n, const double *a, const double *b, double *q, void *stream);
 int k2probe_hypot(int64_t n, const double *a, const double *b, double *h, void *stream);
+/* k2probe_hypotf -- the binary32 correctly rounded hypot, same conventions. */
+int k2probe_hypotf(int64_t n, const float *a, const float *b, float *h, void *stream);
 
 #ifdef __cplusplus
 }

@@ -405,61 +405,71 @@ __device__ __forceinline__ double hypot_cr_body(double x, double y)
 static __device__ __noinline__ uint64_t hypot_cr_bits(uint64_t x, uint64_t y) { return dbits(hypot_cr_body(dfrom(x), dfrom(y))); }
 __device__ __forceinline__ double hypot_cr(double x, double y) { return dfrom(hypot_cr_bits(dbits(x), dbits(y))); }
 
-static __device__ __noinline__ float hypot_cr(float x, float y)
+// floor(sqrt(X)) for an integer X in [2^52, 2^55), and the remainder, on the integer
+// pipes: s0 from the FP32 reciprocal square root of X's leading 31 bits is within 2^6.1 of
+// sqrt(X); one correction s + (X - s0^2) Y 2^-58 (Y = y 2^45 ~ 2^57 / sqrt(X), a 32-bit
+// integer; the residual exact, its leading 31 bits times Y one 32x32->64-bit product) is
+// within 1/2 + 2^-14 (quadratic term 2^-14.8, Y's error 2^-15.5, truncation 2^-23); the
+// sign of X - s^2 then gives floor(sqrt X).
+__device__ __forceinline__ uint32_t isqrt55(uint64_t X, uint64_t &rem)
 {
-    float a = fabsf(x), b = fabsf(y);
-    if (a < b) { float t = a; a = b; b = t; }
-    if (!(a <= 0x1.fffffep127f)) return a + b;
-    if (b == 0.0f) return a;
-    uint32_t ab = fbits(a), bb = fbits(b);
-    int Ea = (int)(ab >> 23), Eb = (int)(bb >> 23);
+    const float xf = __uint2float_rz((uint32_t)(X >> 24));           // [2^28, 2^31)
+    const float y = rsqrtf(xf);                                       // 2^12 / sqrt(X)
+    const int64_t Y = (int64_t)__float2uint_rn(y * 0x1p45f);
+    uint64_t s = __float2uint_rn(xf * y * 4096.0f);
+    int64_t R = (int64_t)(X - s * s);                                 // |R| < 2^34.7
+    s += (uint64_t)(((int64_t)(int32_t)(R >> 4) * Y + (1ll << 53)) >> 54);
+    R = (int64_t)(X - s * s);
+    if (R < 0) { R += (int64_t)(2 * s) - 1; s -= 1; }
+    rem = (uint64_t)R;
+    return (uint32_t)s;
+}
+
+__device__ __forceinline__ float hypot_cr_body(float x, float y)
+{
+    uint32_t ab = fbits(x) & ~F_SIGN, bb = fbits(y) & ~F_SIGN;
+    if (ab < bb) { uint32_t t = ab; ab = bb; bb = t; }
+    if ((ab >> 23) == 0xFF)                                  // inf, or a quiet nan
+        return ffrom((ab << 9) ? (ab | 0x00400000u) : ab);
+    if (bb == 0) return ffrom(ab);
+    const int Ea = (int)(ab >> 23), Eb = (int)(bb >> 23);
     uint32_t A = ab & F_MANT, B = bb & F_MANT;
     int ea, eb;
     if (Ea) { A |= F_HID; ea = Ea - 127; } else { int sh = __clz((int)A) - 8; A <<= sh; ea = -126 - sh; }
     if (Eb) { B |= F_HID; eb = Eb - 127; } else { int sh = __clz((int)B) - 8; B <<= sh; eb = -126 - sh; }
-    if (ea - eb >= 13) return a;
+    if (ea - eb >= 13) return ffrom(ab);
+    uint64_t rem;
     if (Ea == 0) {
-        uint64_t N = (uint64_t)ab * ab + (uint64_t)bb * bb;    // units of 2^-298
-        uint32_t q = (uint32_t)__float2uint_rn(sqrtf(__ull2float_rn(N)));
-        uint64_t N4 = N << 2;
-#pragma unroll 1
-        for (int it = 0; it < 4; ++it) {
-            uint64_t hi = (uint64_t)(2 * q + 1) * (2 * q + 1);
-            if (hi < N4) { ++q; continue; }
-            uint64_t lo = (uint64_t)(2 * q - 1) * (2 * q - 1);
-            if (q > 0 && lo > N4) { --q; continue; }
-            break;
-        }
-        return ffrom(q);
+        // both subnormal: N = (a^2 + b^2) / q^2, q = 2^-149 (N < 2^47), the result
+        // round(sqrt N) q; no ties
+        const uint64_t N = (uint64_t)ab * ab + (uint64_t)bb * bb;
+        const int k = (53 - (63 - __clzll((long long)N))) >> 1;       // N 4^k in [2^52, 2^55)
+        uint32_t q = isqrt55(N << (2 * k), rem) >> k;                 // floor(sqrt N)
+        if (N - (uint64_t)q * q > q) ++q;
+        return ffrom(q);                                            // q < 2^24
     }
-    float as = ffrom((127u << 23) | (A & F_MANT));
-    float bs = ffrom(((uint32_t)(eb - ea + 127) << 23) | (B & F_MANT));
-    float r = sqrtf(fmaf(as, as, bs * bs));
-    uint64_t X = ((uint64_t)A * A) << 6;                       // units of 2^-52
-    uint64_t B2 = (uint64_t)B * B;
-    int sh = 2 * (eb - ea) + 6;
+    // exact a'^2 + b'^2 in units of 2^-52, with a sticky bit for truncated bits of b'^2
+    uint64_t X = ((uint64_t)A * A) << 6;
+    const uint64_t B2 = (uint64_t)B * B;
+    const int sh = 2 * (eb - ea) + 6;
     bool sticky = false;
     if (sh >= 0) X += B2 << sh;
-    else { int k = -sh; sticky = (B2 << (64 - k)) != 0; X += B2 >> k; }
-#pragma unroll 1
-    for (int it = 0; it < 4; ++it) {
-        uint32_t rb = fbits(r);
-        int er = (int)(rb >> 23) - 127;
-        uint64_t R = (rb & F_MANT) | F_HID;
-        uint64_t Mhi = ((2 * R + 1) * (2 * R + 1)) << (2 * er + 4);
-        if (X > Mhi || (X == Mhi && sticky)) { r = ffrom(rb + 1); continue; }
-        if (X == Mhi) { if (R & 1) r = ffrom(rb + 1); break; }
-        uint64_t Mlo = (R == F_HID) ? (((4 * R - 1) * (4 * R - 1)) << (2 * er + 2))
-                                    : (((2 * R - 1) * (2 * R - 1)) << (2 * er + 4));
-        if (X < Mlo) { r = ffrom(rb - 1); continue; }
-        if (X == Mlo && !sticky && (R & 1)) r = ffrom(rb - 1);
-        break;
+    else { const int k = -sh; sticky = (B2 << (64 - k)) != 0; X += B2 >> k; }
+    const uint32_t s = isqrt55(X, rem);                             // sqrt(X) 2^-26 in [1, 2 sqrt 2)
+    const int er = (s >> 27) ? 1 : 0;
+    const int cut = 3 + er;
+    uint32_t R = s >> cut;
+    const bool rb = (s >> (cut - 1)) & 1;
+    const bool st = (s & ((1u << (cut - 1)) - 1)) != 0 || rem != 0 || sticky;
+    int E = ea + er + 127;
+    if (rb && (st || (R & 1))) {
+        ++R;
+        if (R >> 24) { R >>= 1; ++E; }
     }
-    uint32_t rb = fbits(r);
-    int E = (int)(rb >> 23) + ea;
     if (E >= 255) return ffrom(0xFFu << 23);
-    return ffrom(((uint32_t)E << 23) | (rb & F_MANT));
+    return ffrom(((uint32_t)E << 23) | (R & F_MANT));
 }
+static __device__ __noinline__ float hypot_cr(float x, float y) { return hypot_cr_body(x, y); }
 
 // ---------------------------------------------------------------------------------------
 // eq. (EXT) for double: fl(FL(FL(x1 y1 +- x2 y2) / d)) with FL = IEEE binary128 rounding
@@ -595,11 +605,15 @@ __device__ __forceinline__ double ext_num_div(double x1, double y1, double x2, d
 }
 
 // eq. (EXT) for float: the wide type is double, where the products of floats are exact
+// eq. (EXT) for binary32 with binary64 as the wide type: the products are exact in binary64,
+// the sum or difference and the quotient are rounded to binary64, then to binary32.  The
+// quotient uses the FP64 divider: the binary32 kernel leaves the FP64 pipe mostly idle, so
+// that is cheaper here than the integer-pipe division.
 static __device__ __noinline__ float ext_num_div(float x1, float y1, float x2, float y2, bool sub, float d)
 {
     double p2 = (double)x2 * (double)y2;
     double num = fma((double)x1, (double)y1, sub ? -p2 : p2);
-    double q = div_rn(num, (double)d);
+    double q = num / (double)d;
     return __double2float_rn(q);
 }
 

@@ -19,7 +19,7 @@ DEV = "cuda:0"
 def _lib():
     from paper_2407_13116_gb300 import k2svd
     L = k2svd.lib()
-    for f in ("k2probe_div", "k2probe_hypot"):
+    for f in ("k2probe_div", "k2probe_hypot", "k2probe_hypotf"):
         getattr(L, f).argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         getattr(L, f).restype = C.c_int
     return L
@@ -126,6 +126,53 @@ def test_hypot_matches_oracle(case):
         a = (a.view(torch.int64) | (0xFFFFF << 32)).view(torch.float64)
         b = (a.view(torch.int64) - torch.randint(0, 1 << 30, (n,), generator=gen, device=DEV, dtype=torch.int64)).view(torch.float64)
     _check_hypot(a, b, _hyp(L, a, b))
+
+
+def _bits_float(n, gen, elo, ehi, subnormal_frac=0.0):
+    m = torch.randint(0, 1 << 23, (n,), generator=gen, device=DEV, dtype=torch.int32)
+    e = torch.randint(elo + 127, ehi + 128, (n,), generator=gen, device=DEV, dtype=torch.int32)
+    s = torch.randint(0, 2, (n,), generator=gen, device=DEV, dtype=torch.int32)
+    if subnormal_frac:
+        sub = torch.rand(n, generator=gen, device=DEV) < subnormal_frac
+        e = torch.where(sub, torch.zeros_like(e), e)
+        m = torch.where(sub, m | 1, m)
+    return ((s << 31) | (e << 23) | m).view(torch.float32)
+
+
+@pytest.mark.parametrize("case", ["full", "narrow", "ratio_edge", "subnormal", "overflow"])
+def test_hypotf_matches_oracle(case):
+    """The binary32 hypot on 2^22 pairs per case against the oracle's, bit for bit."""
+    import random
+    from test_oracle_hypot import _euclid_ties
+    L = _lib()
+    gen = torch.Generator(device=DEV).manual_seed(17 + (hash(case) & 0xFF))
+    n = 1 << 22
+    if case == "full":
+        a, b = _bits_float(n, gen, -126, 127, 0.05), _bits_float(n, gen, -126, 127, 0.05)
+    elif case == "narrow":
+        a, b = _bits_float(n, gen, -20, 20), _bits_float(n, gen, -30, 20)
+    elif case == "ratio_edge":
+        a = _bits_float(n, gen, -40, 40)
+        d = torch.randint(9, 16, (n,), generator=gen, device=DEV, dtype=torch.int32)
+        b = (_bits_float(n, gen, 0, 0).view(torch.int32) + ((a.view(torch.int32) >> 23 & 0xFF) - 127 - d << 23)).view(torch.float32)
+    elif case == "subnormal":
+        a, b = _bits_float(n, gen, -126, -110, 0.6), _bits_float(n, gen, -126, -110, 0.6)
+    else:
+        a, b = _bits_float(n, gen, 120, 127), _bits_float(n, gen, 115, 127)
+    xs, ys = [], []
+    for (p, q, c) in _euclid_ties(24, 200, random.Random(8)):
+        for sc in (0, -60, 70):
+            xs.append(math.ldexp(p, sc)); ys.append(math.ldexp(q, sc))
+    a = torch.cat([a, torch.tensor(xs, dtype=torch.float32, device=DEV)])
+    b = torch.cat([b, torch.tensor(ys, dtype=torch.float32, device=DEV)])
+    h = torch.empty_like(a)
+    assert L.k2probe_hypotf(a.numel(), a.data_ptr(), b.data_ptr(), h.data_ptr(),
+                            torch.cuda.current_stream().cuda_stream) == 0
+    an, bn = a.cpu().numpy(), b.cpu().numpy()
+    ref = oracle.hypot_n(an, bn, "s", nthreads=os.cpu_count() or 1)
+    got = h.cpu().numpy()
+    bad = got.view(np.int32) != ref.view(np.int32)
+    assert not bad.any(), (an[bad][:4].tolist(), bn[bad][:4].tolist(), got[bad][:4].tolist(), ref[bad][:4].tolist())
 
 
 def test_hypot_exact_ties_and_specials():
