@@ -88,6 +88,19 @@ class Dist:
             self.dist.destroy_process_group()
 
 
+def shard_offset(n_per_rank, rank):
+    """First global matrix index of a rank's contiguous slice: rank r takes matrices
+    [r n, (r+1) n) of one global batch.  The generators are counter-based, so each rank
+    builds exactly its slice and no data moves between ranks."""
+    return rank * n_per_rank
+
+
+def shard_seed(seed, rank):
+    """Seed of a rank's independent batch for the workloads generated per batch (the
+    differentiation and Kogbetliantz sets): distinct per rank, equal to `seed` on rank 0."""
+    return seed + 1000003 * rank
+
+
 # ----------------------------------------------------------------------------------------
 # clock sampling during the timed region
 # ----------------------------------------------------------------------------------------
@@ -228,8 +241,9 @@ def leg(prec, n_half, steps, warmup, dev, D, clocks_index=None):
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
     dt = torch.float64 if prec == "d" else torch.float32
-    G = I.general(n_half, SEED + 2, prec, "wide", xp="torch", device=dev)
-    T3 = I.triangular(n_half, SEED + 3, prec, "wide", xp="torch", device=dev)
+    i0 = shard_offset(n_half, D.rank)          # this rank's slice of the global batch
+    G = I.general(n_half, SEED + 2, prec, "wide", i0=i0, xp="torch", device=dev)
+    T3 = I.triangular(n_half, SEED + 3, prec, "wide", i0=i0, xp="torch", device=dev)
     F, Gu, H = T3[0], T3[1], T3[2]
     Ug = torch.empty((4, n_half), dtype=dt, device=dev); Vg = torch.empty_like(Ug)
     Sg = torch.empty((2, n_half), dtype=dt, device=dev)
@@ -279,7 +293,7 @@ def fwd_bwd_leg(steps, warmup, dev, D, rates, clk_mhz):
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
     n = N_DIFF
-    G = torch.from_numpy(I.rotated(n, SEED + 3)[0]).to(dev)
+    G = torch.from_numpy(I.rotated(n, shard_seed(SEED + 3, D.rank))[0]).to(dev)
     gen = torch.Generator(device=dev).manual_seed(SEED + 3)
     dS = torch.randn((2, n), dtype=torch.float64, device=dev, generator=gen)
     dU = torch.randn((4, n), dtype=torch.float64, device=dev, generator=gen)
@@ -340,8 +354,8 @@ def kog_leg(steps, warmup, dev, D):
     import torch
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
-    orders = I.kog_orders(N_KOG, 8, 128, SEED + 4)
-    flat, _ = I.kog_batch(orders, SEED + 4)
+    orders = I.kog_orders(N_KOG, 8, 128, shard_seed(SEED + 4, D.rank))
+    flat, _ = I.kog_batch(orders, shard_seed(SEED + 4, D.rank))
     A = torch.from_numpy(flat).to(dev)
     n, offs, soffs, tot, stot = k2svd.kog_layout(orders)
     U = torch.empty(tot, dtype=torch.float64, device=dev); V = torch.empty_like(U)
@@ -394,7 +408,8 @@ def phases_leg(steps, warmup, dev, D, rates, clk_mhz, oc):
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
     n = N_HALF_D
-    G = I.general(n, SEED + 2, "d", "wide", xp="torch", device=dev)
+    i0 = shard_offset(n, D.rank)
+    G = I.general(n, SEED + 2, "d", "wide", i0=i0, xp="torch", device=dev)
     Gs = torch.empty_like(G)
     res = {}
 
@@ -420,7 +435,7 @@ def phases_leg(steps, warmup, dev, D, rates, clk_mhz, oc):
                                      "algorithmic_bytes": nbytes, "peak_source": hbm_src},
                         "workload": "2^27 wide-range FP64 general matrices, extra = 1 (G in 32 B, Gs out 32 B, s, types)"}
     del G, Gs
-    T3 = I.triangular(n, SEED + 3, "d", "wide", xp="torch", device=dev)
+    T3 = I.triangular(n, SEED + 3, "d", "wide", i0=i0, xp="torch", device=dev)
     outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(6)]
     L = k2svd.lib()
     ptrs = [o.data_ptr() for o in outs]
@@ -438,7 +453,7 @@ def phases_leg(steps, warmup, dev, D, rates, clk_mhz, oc):
     return res
 
 
-def e2e_leg(steps, warmup, dev):
+def e2e_leg(steps, warmup, dev, D):
     """End to end through the Python API: pinned host inputs -> device -> kernels -> host
     outputs, in chunks over three streams with a buffer set each, so that the host-to-device
     copy of one chunk, the kernel of another and the device-to-host copy of a third run at
@@ -454,8 +469,9 @@ def e2e_leg(steps, warmup, dev):
     def chunked(x):       # (k, n) -> (nc, k, c): every chunk one contiguous block
         return x.reshape(x.shape[0], nc, c).permute(1, 0, 2).contiguous()
 
-    Gh = chunked(I.general(n, SEED + 2, "d", "wide", xp="torch", device=dev)).cpu().pin_memory()
-    Th = chunked(I.triangular(n, SEED + 3, "d", "wide", xp="torch", device=dev)).cpu().pin_memory()
+    i0 = shard_offset(n, D.rank)
+    Gh = chunked(I.general(n, SEED + 2, "d", "wide", i0=i0, xp="torch", device=dev)).cpu().pin_memory()
+    Th = chunked(I.triangular(n, SEED + 3, "d", "wide", i0=i0, xp="torch", device=dev)).cpu().pin_memory()
     outs = {k: torch.empty((nc, rows, c), dtype=dt, pin_memory=True) for k, rows in
             (("Ug", 4), ("Vg", 4), ("Sg", 2), ("Ut", 4), ("Vt", 4), ("St", 2))}
     streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
@@ -492,13 +508,14 @@ def e2e_leg(steps, warmup, dev):
 
     for _ in range(warmup):
         step()
+    D.barrier()
     t = time.perf_counter()
     for _ in range(steps):
         step()
-    el = (time.perf_counter() - t) / steps
+    el = D.max((time.perf_counter() - t) / steps)
     h2d = (4 + 3) * 8 * n
     d2h = 2 * (4 + 4 + 2) * 8 * n
-    return {"value": 2 * n / el, "unit": "SVDs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+    return {"value": D.world * 2 * n / el, "unit": "SVDs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "batch": 2 * n, "ms_per_step": el * 1e3, "streams": NS, "chunk": c}
 
 
@@ -567,7 +584,7 @@ def run_ours(a):
                                   "(k2svd_dtrsvd2) per GPU, exponents uniform in [-1021,1021], 2% subnormal or "
                                   "near-overflow entries, SoA planes",
                       "matrices_per_gpu_per_step": 2 * N_HALF_D, "l2": "inputs (7.5 GB) larger than L2",
-                      "parallelism": "replicas (weak scaling, no collective)"},
+                      "parallelism": "one slice of the global batch per rank (weak scaling, no collective)"},
            "clocks": res["clocks"], "gpu_launches": res["launches"], "roofline": roofline,
            "pipe_rates": rates}
     if not a.no_fp32:
@@ -590,7 +607,7 @@ def run_ours(a):
     if not a.no_kog:
         out["kogbet"] = kog_leg(max(2, a.steps // 3), 1, dev, D)
     if D.world == 1 and not a.no_e2e:
-        out["e2e"] = e2e_leg(max(2, a.steps // 3), 1, dev)
+        out["e2e"] = e2e_leg(max(2, a.steps // 3), 1, dev, D)
     if D.rank == 0 and D.world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     D.close()
