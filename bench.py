@@ -515,8 +515,20 @@ def e2e_leg(steps, warmup, dev, D):
     el = D.max((time.perf_counter() - t) / steps)
     h2d = (4 + 3) * 8 * n
     d2h = 2 * (4 + 4 + 2) * 8 * n
+    # the host link's own copy rates on this machine (one pinned 1 GiB copy each way), for reading
+    # the end-to-end number: with these copies overlapped it is bound by the larger of
+    # h2d / h2d rate and d2h / d2h rate
+    link = {}
+    x = outs["Ug"].view(-1)[: 1 << 27]
+    y = torch.empty(x.numel(), dtype=dt, device=dev)
+    for name, fn in (("h2d_gbs", lambda: y.copy_(x, non_blocking=True)), ("d2h_gbs", lambda: x.copy_(y, non_blocking=True))):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(); fn(); e1.record(); torch.cuda.synchronize()
+        link[name] = x.numel() * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9
     return {"value": D.world * 2 * n / el, "unit": "SVDs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "batch": 2 * n, "ms_per_step": el * 1e3, "streams": NS, "chunk": c}
+            "batch": 2 * n, "ms_per_step": el * 1e3, "streams": NS, "chunk": c, "link": link,
+            "copy_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6}
 
 
 def cpu_baseline(seconds=10.0):
