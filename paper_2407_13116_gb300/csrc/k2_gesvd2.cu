@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(128, 8) svd2_kernel(const svd_args<T> a)
         const T g22 = a.g3[i];
         svd2_out<T> o;
         if (is_fin(g11) && is_fin(g21) && is_fin(g12) && is_fin(g22)) {
-            svd2<T>(g11, g21, g12, g22, o);
+            svd2<T, !TRI>(g11, g21, g12, g22, o);              // general matrices leave the FP64 pipe room
         } else {
             const T qn = T(NAN);
             o.U.a11 = o.U.a21 = o.U.a12 = o.U.a22 = qn;

@@ -145,8 +145,12 @@ template <typename T> struct tri_out {
     ef<T> s1, s2;
 };
 
+// The cos/sin divisions of the triangular SVD: on the FP64 divider when FDIV (the caller's
+// FP64 pipe has room: general matrices), else as every other division.  Same results.
+template <bool FDIV, typename T> __device__ __forceinline__ T csdiv(T a, T b) { return FDIV ? a / b : qdiv(a, b); }
+
 // Alg. 1 and Alg. 2 on R = [[r11, r12], [0, r22]] (all > 0), with the transpose-swap of eq. (RT)
-template <typename T>
+template <typename T, bool FDIV = false>
 __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int &flags)
 {
     z.swap = pos_lt(r11, r22);
@@ -178,8 +182,8 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
     else tf = qdiv(t2, T(1) + hypot_cr(t2, T(1)));           // eq. (tf)
     T secf = hypot_cr(tf, T(1));
     z.tanphi = tf;
-    z.cphi = qdiv(T(1), secf);
-    z.sphi = qdiv(tf, secf);
+    z.cphi = csdiv<FDIV>(T(1), secf);
+    z.sphi = csdiv<FDIV>(tf, secf);
     // Alg. 2
     T t = fma(rc, tf, rb);                                 // eq. (tp)
     T tp = qdiv(t, ra);
@@ -194,8 +198,8 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
         flags |= FL_TPINF;
     } else {                                               // eq. (s')
         T secp = hypot_cr(tp, T(1));
-        z.cpsi = qdiv(T(1), secp);
-        z.spsi = qdiv(tp, secp);
+        z.cpsi = csdiv<FDIV>(T(1), secp);
+        z.spsi = csdiv<FDIV>(tp, secp);
         ef<T> sf = ef_div(ef_of(secf), ef_of(secp));
         s1 = ef_div(era, sf);
         s2 = ef_mul(erc, sf);
@@ -247,7 +251,8 @@ __device__ __forceinline__ void phase1(T &g11, T &g21, T &g12, T &g22, int extra
     tp = !eq0(g11) | (!eq0(g21) << 1) | (!eq0(g12) << 2) | (!eq0(g22) << 3);
 }
 
-template <typename T>
+// FDIV: see csdiv; the results do not depend on it.
+template <typename T, bool FDIV = false>
 __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
 {
     int t, s, tp, flags = 0;
@@ -273,7 +278,7 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
         bool n12 = lt0(b); b = absv(b); if (n12) d = ngt(d);
         bool n22 = lt0(d); d = absv(d);
         tri_out<T> z;
-        tri_svd(a, b, d, z, flags);
+        tri_svd<T, FDIV>(a, b, d, z, flags);
         m22<T> U = ucheck(z);                              // U = P_U S11 S22 U-check
         if (n11) neg_row(U, 0);
         if (n22) neg_row(U, 1);
@@ -340,7 +345,7 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
             bool n22 = lt0(r22);
             if (n22) r22 = ngt(r22);                           // S22 R'
             tri_out<T> z;
-            tri_svd(r11, r12, r22, z, flags);
+            tri_svd<T, FDIV>(r11, r12, r22, z, flags);
             m22<T> V = vcheck(z);                          // V = P_V S12 V-check
             if (n12) neg_row(V, 1);
             if (pv) swap_rows(V);
