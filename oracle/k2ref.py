@@ -69,6 +69,7 @@ def lib():
                 getattr(L, "k2ref_hypot_n_" + sfx).argtypes = [I64, P, P, P, C.c_int]
                 getattr(L, "k2ref_prescale2_" + sfx).argtypes = [I64, P, I64, P, I64, P, P, I32, C.c_int]
                 getattr(L, "k2ref_lasv2_" + sfx).argtypes = [I64, P, P, P, P, P, P, P, P, P, C.c_int]
+                getattr(L, "k2ref_cgesvd2_" + sfx).argtypes = [I64, P, I64, P, I64, P, I64, P, I64, P, C.c_int]
                 fn.restype = T
                 getattr(L, "k2ref_trace_" + sfx).argtypes = [P, P, P]
                 getattr(L, "k2ref_efops_" + sfx).argtypes = [T, T, P, P]
@@ -182,6 +183,20 @@ def lasv2(F, Gp, H, prec="d", nthreads=1):
     if rc != 0:
         raise ValueError("k2ref_lasv2 returned %d" % rc)
     return tuple(out)
+
+
+def cgesvd2(G, prec="d", nthreads=1):
+    """SVD of complex 2x2 matrices (Sect. 3.4) given as 8 planes G[8, n]: (re, im) of g11, g21,
+    g12, g22.  Returns U, V (8, n) in the same layout, S (2, n) and info (n,)."""
+    T = _dt(prec)
+    G = np.ascontiguousarray(G, dtype=T)
+    n = G.shape[1]
+    U = np.empty((8, n), T); V = np.empty((8, n), T); S = np.empty((2, n), T); info = np.empty(n, np.int32)
+    rc = getattr(lib(), "k2ref_cgesvd2_" + prec)(n, _ptr(G), n, _ptr(U), n, _ptr(V), n, _ptr(S), n, _ptr(info),
+                                                  int(nthreads))
+    if rc != 0:
+        raise ValueError("k2ref_cgesvd2 returned %d" % rc)
+    return U, V, S, info
 
 
 def trace(g, prec="d"):
