@@ -30,6 +30,7 @@ N_HALF_S = 1 << 28
 E2E_HALF = 1 << 25
 N_DIFF = 1 << 24
 N_KOG = 8192
+N_COMPLEX = 1 << 26
 E2E_CHUNK = 1 << 21
 METRIC = "FP64 2×2 SVDs/s & % of roofline; fwd+bwd/s; batched Kogbetliantz speedup"
 BYTES_GE = {"d": 112, "s": 56}          # in 4 T + out (4 U + 4 V + 2 S) T
@@ -48,6 +49,7 @@ def parse():
     p.add_argument("--no-fwd-bwd", action="store_true")
     p.add_argument("--no-kog", action="store_true")
     p.add_argument("--no-phases", action="store_true")
+    p.add_argument("--no-complex", action="store_true")
     p.add_argument("--profile-case", choices=["d", "s", "kog"], default=None,
                    help="run a small case of the 2x2 kernels or of the persistent Kogbetliantz "
                         "kernel (for ncu captures) and exit")
@@ -453,6 +455,45 @@ def phases_leg(steps, warmup, dev, D, rates, clk_mhz, oc):
     return res
 
 
+def complex_leg(steps, warmup, dev, D, rates, clk_mhz, oc):
+    """The complex 2x2 SVD (k2svd_zgesvd2, Sect. 3.4) on 2^26 double complex matrices whose
+    real and imaginary planes are two wide-range streams."""
+    import torch
+    from paper_2407_13116_gb300 import inputs as I
+    from paper_2407_13116_gb300 import k2svd
+    n = N_COMPLEX
+    i0 = shard_offset(n, D.rank)
+    G = torch.empty((8, n), dtype=torch.float64, device=dev)
+    G[0::2] = I.general(n, SEED + 6, "d", "wide", i0=i0, xp="torch", device=dev)
+    G[1::2] = I.general(n, SEED + 7, "d", "wide", i0=i0, xp="torch", device=dev)
+    U = torch.empty((8, n), dtype=torch.float64, device=dev); V = torch.empty_like(U)
+    S = torch.empty((2, n), dtype=torch.float64, device=dev)
+    fn = lambda: k2svd.cgesvd2(G, U=U, V=V, S=S, want_info=False)
+    for _ in range(warmup):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    D.barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = D.max(e0.elapsed_time(e1) / steps)
+    cost = slot_costs(oc["wide_d_cgesvd2"], rates, "d")["fp64"]
+    peak = fp64_peak(clk_mhz)
+    hbm, _ = hbm_peak_gbs()
+    nbytes = (64 + 64 + 64 + 16) * n
+    del G, U, V, S
+    torch.cuda.empty_cache()
+    return {"value": D.world * n / (ms / 1e3), "unit": "SVDs/s", "ms": ms,
+            "roofline": {"bound": "alu", "achieved": n * cost / (ms / 1e3) / 1e9, "peak": peak / 1e9,
+                         "unit": "G FP64-pipe op/s", "frac": n * cost / (ms / 1e3) / peak, "ops_per_matrix": cost,
+                         "algorithmic_bytes": nbytes, "hbm_frac": nbytes / (ms / 1e3) / (hbm * 1e9)},
+            "workload": "2^26 double complex 2x2 matrices, real and imaginary parts wide-range (exponents "
+                        "uniform in [-1021,1021], 2% subnormal or near-overflow); 208 B per matrix"}
+
+
 def e2e_leg(steps, warmup, dev, D):
     """End to end through the Python API: pinned host inputs -> device -> kernels -> host
     outputs, in chunks over three streams with a buffer set each, so that the host-to-device
@@ -616,6 +657,8 @@ def run_ours(a):
         out["fwd_bwd"] = fwd_bwd_leg(a.steps, a.warmup, dev, D, rates, clk_mhz)
     if not a.no_phases:
         out["phases"] = phases_leg(a.steps, a.warmup, dev, D, rates, clk_mhz, oc)
+    if not a.no_complex:
+        out["complex"] = complex_leg(a.steps, a.warmup, dev, D, rates, clk_mhz, oc)
     if not a.no_kog:
         out["kogbet"] = kog_leg(max(2, a.steps // 3), 1, dev, D)
     if D.world == 1 and not a.no_e2e:

@@ -100,6 +100,35 @@ int k2svd_strsvd2(int64_t batch, const float *F, const float *Gu, const float *H
                   int32_t *info, void *stream);
 
 /*
+ * k2svd_zgesvd2 / k2svd_cgesvd2 -- SVD of `batch` complex 2x2 matrices (Sect. 3.4),
+ * G = U diag(sigma1, sigma2) V^H with U, V unitary and sigma1 >= sigma2 >= 0.  A real G
+ * (every imaginary part zero) gets the real method (k2svd_?gesvd2's results, imaginary parts
+ * zero); a purely imaginary G = iH the real method on H with U = i U_H.  Otherwise the
+ * matrix is prescaled over every real and imaginary component with the scale type raised by
+ * one; a matrix with at most three nonzero elements is made real by row and column phases
+ * conj(z)/|z|; a matrix without zeros is reduced as in Sect. 3.2.2 with complex column
+ * norms, row phases that make the first column real, the real rotation (no (EXT), item 3)
+ * and phases that make r12 and r22 real; the real method then runs on the real matrix and
+ * U, V are formed by real-complex products.  Complex product (a,b)(c,d) is
+ * (fma(a,c,-(b d)), fma(a,d,b c)) and |z| the correctly rounded hypot, so results are
+ * bitwise reproducible.
+ *
+ *   batch        number of matrices, >= 0
+ *   G, ldg       8 planes: (re, im) of g11, g21, g12, g22; ldg >= batch
+ *   U, ldu       8 planes, same layout; V, ldv likewise
+ *   S, lds       2 planes: sigma1, sigma2
+ *   info         nullable int32 plane: t | t' << 4 | flags << 8 (flags of the real method,
+ *                plus 0x100 for a purely imaginary G and 0x200 for the complex reduction;
+ *                an element is nonzero when either part is); -1 for non-finite input (NaN
+ *                outputs for that matrix)
+ * Argument order for error codes: 1 batch, 2 G, 3 ldg, 4 U, 5 ldu, 6 V, 7 ldv, 8 S, 9 lds.
+ */
+int k2svd_zgesvd2(int64_t batch, const double *G, int64_t ldg, double *U, int64_t ldu, double *V, int64_t ldv,
+                  double *S, int64_t lds, int32_t *info, void *stream);
+int k2svd_cgesvd2(int64_t batch, const float *G, int64_t ldg, float *U, int64_t ldu, float *V, int64_t ldv,
+                  float *S, int64_t lds, int32_t *info, void *stream);
+
+/*
  * k2svd_dprescale2 / k2svd_sprescale2 -- phase 1 of the method on its own (Sect. 3.1,
  * eqs. (eG), (s); the phases "can be used on their own", Sect. 5): for each matrix the type
  * t (bit k set when element k of (g11, g21, g12, g22) is nonzero), the exponent

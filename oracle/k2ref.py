@@ -232,13 +232,17 @@ def ext(x1, y1, x2, y2, neg, d, sec, prec="d"):
 OPS = ("add", "mul", "fma", "div", "hypot", "ext")
 
 
-def opcount(G, prec="d", triangular=False):
+def opcount(G, prec="d", triangular=False, complex_planes=False):
     """Mean algorithmic operation counts per matrix of the method on a batch (one thread):
-    {add, mul, fma, div, hypot, ext} (exact scalings, comparisons and sign changes excluded)."""
+    {add, mul, fma, div, hypot, ext} (exact scalings, comparisons and sign changes excluded).
+    complex_planes: G is 8 planes of complex matrices (Sect. 3.4)."""
     L = lib()
     buf = np.zeros(6, np.int64)
     L.k2ref_opcount(1 if prec == "d" else 0, _ptr(buf), 1)
-    if triangular:
+    if complex_planes:
+        cgesvd2(G, prec, nthreads=1)
+        n = G.shape[1]
+    elif triangular:
         trsvd2(G[0], G[1], G[2], prec, nthreads=1)
         n = G.shape[1]
     else:

@@ -49,6 +49,10 @@ def _bind_extra(L):
     L.k2svd_dgesvd2_bwd.restype = C.c_int
     L.k2svd_sgesvd2_bwd.argtypes = [I64, P, P, P, I64, P, P, P, P, F, P]
     L.k2svd_sgesvd2_bwd.restype = C.c_int
+    for p in ("z", "c"):
+        f = getattr(L, "k2svd_%sgesvd2" % p)
+        f.argtypes = [I64, P, I64, P, I64, P, I64, P, I64, P, P]
+        f.restype = C.c_int
     for p, T in (("d", D), ("s", F)):
         f = getattr(L, "k2svd_%sprescale2" % p)
         f.argtypes = [I64, P, I64, P, I64, P, P, I32, P]
@@ -167,6 +171,45 @@ def trsvd2(F, Gu, H, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_e
     if rc != 0:
         raise K2SVDError("k2svd_%strsvd2 returned %d" % (p, rc))
     return U, V, S, Se, Sf, info
+
+
+def cgesvd2(G, U=None, V=None, S=None, want_info=True):
+    """SVD of complex 2x2 matrices (k2svd_zgesvd2 / k2svd_cgesvd2).  G is (8, n) real planes
+    (re, im of g11, g21, g12, g22) of float64 or float32; returns (U, V, S, info) with U, V
+    (8, n) in the same layout and S (2, n).  See complex_to_planes / planes_to_complex."""
+    p = {"d": "z", "s": "c"}[_prefix(G.dtype)]
+    dev = G.device
+    _check(G, "G", G.dtype, dev)
+    n = G.shape[1]
+    ldg = _planes(G, 8, "G")
+    U = torch.empty((8, n), dtype=G.dtype, device=dev) if U is None else U
+    V = torch.empty((8, n), dtype=G.dtype, device=dev) if V is None else V
+    S = torch.empty((2, n), dtype=G.dtype, device=dev) if S is None else S
+    info = torch.empty((n,), dtype=torch.int32, device=dev) if want_info else None
+    for t, nm, k in ((U, "U", 8), (V, "V", 8), (S, "S", 2)):
+        _check(t, nm, G.dtype, dev)
+    ldu, ldv, lds = _planes(U, 8, "U"), _planes(V, 8, "V"), _planes(S, 2, "S")
+    with torch.cuda.device(dev):
+        rc = getattr(lib(), "k2svd_%sgesvd2" % p)(n, _ptr(G), ldg, _ptr(U), ldu, _ptr(V), ldv, _ptr(S), lds,
+                                                  _ptr(info), _stream())
+    if rc != 0:
+        raise K2SVDError("k2svd_%sgesvd2 returned %d" % (p, rc))
+    return U, V, S, info
+
+
+def complex_to_planes(A):
+    """(..., 2, 2) complex tensor -> (8, n) real planes (re, im of a11, a21, a12, a22)."""
+    A = A.reshape(-1, 2, 2)
+    X = torch.stack([A[:, 0, 0], A[:, 1, 0], A[:, 0, 1], A[:, 1, 1]])
+    return torch.stack([X.real, X.imag], dim=1).reshape(8, -1).contiguous()
+
+
+def planes_to_complex(X, shape=None):
+    """(8, n) real planes -> (n, 2, 2) complex tensor (or `shape` + (2, 2))."""
+    Y = X.reshape(4, 2, -1)
+    Z = torch.complex(Y[:, 0], Y[:, 1])
+    A = torch.stack([torch.stack([Z[0], Z[2]], -1), torch.stack([Z[1], Z[3]], -1)], -2)
+    return A if shape is None else A.reshape(tuple(shape) + (2, 2))
 
 
 def prescale2(G, extra=0, Gs=None, want_types=True):

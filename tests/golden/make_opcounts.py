@@ -10,6 +10,8 @@ import json
 import os
 import sys
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
@@ -29,6 +31,11 @@ def main():
             I.triangular(SAMPLE, SEED + 3, prec, "wide"), prec, triangular=True)
         out["workloads"]["narrow_%s_gesvd2" % prec] = oracle.opcount(
             I.general(SAMPLE, SEED + 1, prec, "narrow"), prec)
+        # complex matrices (Sect. 3.4): real and imaginary planes from two wide-range streams
+        G8 = np.empty((8, SAMPLE), np.float64 if prec == "d" else np.float32)
+        G8[0::2] = I.general(SAMPLE, SEED + 6, prec, "wide")
+        G8[1::2] = I.general(SAMPLE, SEED + 7, prec, "wide")
+        out["workloads"]["wide_%s_cgesvd2" % prec] = oracle.opcount(G8, prec, complex_planes=True)
     with open(os.path.join(HERE, "opcounts.json"), "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
         f.write("\n")
