@@ -53,7 +53,7 @@ template <typename T> __device__ __forceinline__ void swap_cols(m22<T> &m)
 }
 // IEEE negation (a sign-bit flip) on the integer pipes
 __device__ __forceinline__ double ngt(double x) { return dfrom(dbits(x) ^ D_SIGN); }
-__device__ __forceinline__ float ngt(float x) { return ffrom(fbits(x) ^ F_SIGN); }
+__device__ __forceinline__ float ngt(float x) { return -x; }
 template <typename T> __device__ __forceinline__ void neg_row(m22<T> &m, int r)
 {
     if (r == 0) { m.a11 = ngt(m.a11); m.a12 = ngt(m.a12); } else { m.a21 = ngt(m.a21); m.a22 = ngt(m.a22); }
