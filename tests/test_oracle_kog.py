@@ -12,7 +12,7 @@ EPS = 2.0 ** -52
 
 
 def test_order_two_is_the_2x2_method():
-    # exponent spreads below 1000, so the driver's power-of-two prescaling stays exact
+    # exponent spreads below 1000, so the n x n method's power-of-two prescaling stays exact
     G = np.concatenate([I.general(200, 91, "d", "narrow"), I.safe_range(200, 92, 1043)], axis=1)
     r = oracle.gesvd2(G)
     for i in range(G.shape[1]):
