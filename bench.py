@@ -50,9 +50,9 @@ def parse():
     p.add_argument("--no-kog", action="store_true")
     p.add_argument("--no-phases", action="store_true")
     p.add_argument("--no-complex", action="store_true")
-    p.add_argument("--profile-case", choices=["d", "s", "kog"], default=None,
-                   help="run a small case of the 2x2 kernels or of the persistent Kogbetliantz "
-                        "kernel (for ncu captures) and exit")
+    p.add_argument("--profile-case", choices=["d", "s", "kog", "z"], default=None,
+                   help="run a small case of the 2x2 kernels (d, s), of the complex kernel (z) or "
+                        "of the persistent Kogbetliantz kernel (kog), for ncu captures, and exit")
     p.add_argument("--profile-n", type=int, default=1 << 22)
     return p.parse_args()
 
@@ -160,8 +160,8 @@ class Clocks:
 # dram__bytes_write.sum) of `python bench.py --profile-case d` (2^22 matrices), scaled by
 # the matrix count to a full 2^27-matrix launch.  Valid only for the kernel sources with
 # this hash; any change to them reports null until a new capture is taken.
-TRAFFIC_SRC_HASH = "103f02eac2d217a8"
-TRAFFIC_BYTES_PER_MATRIX = (134.307328e6 + 284.688640e6) / (1 << 22)
+TRAFFIC_SRC_HASH = "92a0114ef9e874a3"
+TRAFFIC_BYTES_PER_MATRIX = (134.417664e6 + 284.337664e6) / (1 << 22)
 KERNEL_SOURCES = ("k2_fp.cuh", "k2_svd2.cuh", "k2_gesvd2.cu")
 
 
@@ -718,6 +718,17 @@ def profile_case(a):
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
     dev = torch.device("cuda", 0)
+    if a.profile_case == "z":
+        n = a.profile_n
+        G = torch.empty((8, n), dtype=torch.float64, device=dev)
+        G[0::2] = I.general(n, SEED + 6, "d", "wide", xp="torch", device=dev)
+        G[1::2] = I.general(n, SEED + 7, "d", "wide", xp="torch", device=dev)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            k2svd.cgesvd2(G, want_info=False)
+        torch.cuda.synchronize()
+        print("profile case z n=%d done" % n)
+        return
     if a.profile_case == "kog":
         orders = I.kog_orders(304, 8, 128, SEED + 4)
         flat, _ = I.kog_batch(orders, SEED + 4)
