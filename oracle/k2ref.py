@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libk2ref.so")
-_SRC = [os.path.join(_HERE, f) for f in ("k2ref.c", "k2ref_body.inc", "k2ref_kog.c", "k2ref_bwd.c")]
+_SRC = [os.path.join(_HERE, f) for f in ("k2ref.c", "k2ref_body.inc", "k2ref_kog.c", "k2ref_bwd.c", "k2ref_rect.c")]
 _lock = threading.Lock()
 _lib = None
 
@@ -279,6 +279,25 @@ def kogbet(A, prec="d", max_sweeps=40, tol_factor=1.0):
                                                  float(tol_factor), C.byref(sw), C.byref(info))
     if rc != 0:
         raise ValueError("k2ref_kogbet returned %d" % rc)
+    return U, S, V, sw.value, info.value
+
+
+def gesvdr(A, prec="d", max_sweeps=40, tol_factor=1.0):
+    """SVD of one rectangular m x n matrix by QR with column pivoting to a square one and the
+    n x n Kogbetliantz method (Sect. 1): returns (U (m x k), S (k), V (n x k), sweeps, info),
+    k = min(m, n), A ~ U diag(S) V^T."""
+    T = _dt(prec)
+    A = np.asfortranarray(A, dtype=T)
+    m, n = A.shape
+    k = min(m, n)
+    U = np.empty((m, k), T, order="F"); V = np.empty((n, k), T, order="F"); S = np.empty(k, T)
+    sw = C.c_int32(0); info = C.c_int32(0)
+    fn = getattr(lib(), "k2ref_gesvdr_" + prec)
+    fn.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                   C.c_void_p, C.c_void_p]
+    rc = fn(m, n, _ptr(A), _ptr(U), _ptr(V), _ptr(S), int(max_sweeps), float(tol_factor), C.byref(sw), C.byref(info))
+    if rc != 0:
+        raise ValueError("k2ref_gesvdr returned %d" % rc)
     return U, S, V, sw.value, info.value
 
 
