@@ -31,6 +31,7 @@ E2E_HALF = 1 << 25
 N_DIFF = 1 << 24
 N_KOG = 8192
 N_COMPLEX = 1 << 26
+N_RECT = 2048
 E2E_CHUNK = 1 << 21
 METRIC = "FP64 2×2 SVDs/s & % of roofline; fwd+bwd/s; batched Kogbetliantz speedup"
 BYTES_GE = {"d": 112, "s": 56}          # in 4 T + out (4 U + 4 V + 2 S) T
@@ -50,6 +51,7 @@ def parse():
     p.add_argument("--no-kog", action="store_true")
     p.add_argument("--no-phases", action="store_true")
     p.add_argument("--no-complex", action="store_true")
+    p.add_argument("--no-rect", action="store_true")
     p.add_argument("--profile-case", choices=["d", "s", "kog", "z"], default=None,
                    help="run a small case of the 2x2 kernels (d, s), of the complex kernel (z) or "
                         "of the persistent Kogbetliantz kernel (kog), for ncu captures, and exit")
@@ -494,6 +496,68 @@ def complex_leg(steps, warmup, dev, D, rates, clk_mhz, oc):
                         "uniform in [-1021,1021], 2% subnormal or near-overflow); 208 B per matrix"}
 
 
+def rect_leg(steps, warmup, dev, D, rates, clk_mhz):
+    """Rectangular matrices (k2svd_dgesvdr: QR with column pivoting to square, the n x n
+    Kogbetliantz driver, U = Q U_R): 2048 FP64 matrices with n uniform in {8..128} and m
+    uniform in {n..3n}, N(0,1) entries."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    from paper_2407_13116_gb300 import inputs as I
+    from paper_2407_13116_gb300 import k2svd
+    seed = shard_seed(SEED + 8, D.rank)
+    n = I.kog_orders(N_RECT, 8, 128, seed)
+    m = (n + np.floor(I.uniform01(N_RECT, seed, 9) * (2 * n + 1))).astype(np.int32)
+    shapes = np.stack([m, n], 1)
+    mm, nn, ao, uo, vo, so, (na, nu, nv, ns) = k2svd.rect_layout(shapes)
+    A = torch.from_numpy(I.normal(na, seed, 10)).to(dev)
+    U = torch.empty(nu, dtype=torch.float64, device=dev); V = torch.empty(nv, dtype=torch.float64, device=dev)
+    S = torch.empty(ns, dtype=torch.float64, device=dev)
+    sw = torch.empty(N_RECT, dtype=torch.int32, device=dev); info = torch.empty_like(sw)
+    L = k2svd.lib()
+    wsb = C.c_size_t(0)
+    assert L.k2svd_dgesvdr_ws(N_RECT, mm.ctypes.data, nn.ctypes.data, 0, C.byref(wsb)) == 0
+    ws = torch.empty(wsb.value + 256, dtype=torch.uint8, device=dev)
+    wp = C.c_void_p((ws.data_ptr() + 255) // 256 * 256)
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args = (N_RECT, mm.ctypes.data, nn.ctypes.data, ao.ctypes.data, uo.ctypes.data, vo.ctypes.data, so.ctypes.data,
+            A.data_ptr(), U.data_ptr(), V.data_ptr(), S.data_ptr(), sw.data_ptr(), info.data_ptr(), 40, 1.0, 0,
+            wp, wsb.value, st)
+    fn = lambda: L.k2svd_dgesvdr(*args)
+    for _ in range(max(warmup, 1)):
+        assert fn() == 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    D.barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = D.max(e0.elapsed_time(e1) / steps)
+    sweeps = sw.cpu().numpy().astype(np.float64)
+    p_, q_ = np.maximum(m, n).astype(np.float64), np.minimum(m, n).astype(np.float64)
+    wd = rates["dfma"] / rates["ddiv"]
+    ops = 0.0
+    for p1, q1, s1 in zip(p_, q_, sweeps):
+        j = np.arange(q1)
+        ops += float(((q1 - j) * (p1 - j)).sum())                              # column norms
+        ops += float(((q1 - j - 1) * (2 * (p1 - j) + wd)).sum())               # reflector applications
+        ops += float((q1 * (2 * (p1 - j) + wd)).sum())                         # Q
+        ops += s1 * (q1 * (q1 - 1) / 2) * (16 * q1 + 239)                      # Kogbetliantz sweeps
+        ops += p1 * q1 * q1                                                     # Q U_R
+    peak = fp64_peak(clk_mhz)
+    conv = int((info.cpu().numpy() == 0).sum())
+    del A, U, V, S, ws
+    torch.cuda.empty_cache()
+    return {"value": D.world * N_RECT / (ms / 1e3), "unit": "matrices/s", "ms": ms, "converged": conv,
+            "mean_sweeps": float(sweeps.mean()),
+            "roofline": {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e9, "peak": peak / 1e9,
+                         "unit": "G FP64-pipe op/s", "frac": ops / (ms / 1e3) / peak, "ops": ops},
+            "workload": "2048 FP64 m x n matrices, n uniform in {8..128}, m uniform in {n..3n}, N(0,1) entries; "
+                        "QR with column pivoting, the n x n Kogbetliantz driver, U = Q U_R"}
+
+
 def e2e_leg(steps, warmup, dev, D):
     """End to end through the Python API: pinned host inputs -> device -> kernels -> host
     outputs, in chunks over three streams with a buffer set each, so that the host-to-device
@@ -659,6 +723,8 @@ def run_ours(a):
         out["phases"] = phases_leg(a.steps, a.warmup, dev, D, rates, clk_mhz, oc)
     if not a.no_complex:
         out["complex"] = complex_leg(a.steps, a.warmup, dev, D, rates, clk_mhz, oc)
+    if not a.no_rect:
+        out["rect"] = rect_leg(max(1, a.steps // 5), 1, dev, D, rates, clk_mhz)
     if not a.no_kog:
         out["kogbet"] = kog_leg(max(2, a.steps // 3), 1, dev, D)
     if D.world == 1 and not a.no_e2e:

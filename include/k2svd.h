@@ -100,6 +100,46 @@ int k2svd_strsvd2(int64_t batch, const float *F, const float *Gu, const float *H
                   int32_t *info, void *stream);
 
 /*
+ * k2svd_dgesvdr_ws / k2svd_sgesvdr_ws, k2svd_dgesvdr / k2svd_sgesvdr -- SVD of `batch`
+ * rectangular matrices of uneven shapes, A_i = U_i diag(S_i) V_i^T with k = min(m, n)
+ * singular values (Sect. 1: an m x n matrix, m > n, is first reduced to a square one by a
+ * URV-type factorization such as QR with column pivoting; for m < n the transpose is
+ * decomposed).  B = A (or A^T), p x q with p >= q, is scaled by the power of two that puts
+ * its largest element in [1/2, 1); Householder QR with column pivoting B P = Q R (squared
+ * column norms recomputed at every step by fma in increasing row order, the first column of
+ * largest norm as pivot, alpha = -sign(x0) ||x||, v0 = x0 - alpha,
+ * v^T v = 2 ||x|| (||x|| + |x0|), each column updated with f = (s + s) / v^T v); R (q x q)
+ * goes through the n x n Kogbetliantz driver (k2svd_?kogbet, same max_sweeps, tol_factor
+ * and sweeps/info semantics); U = Q U_R, V = P V_R (exchanged for m < n).  Results are
+ * bitwise reproducible.  The paper's "dynamic ordering" of pivots is not implemented (the
+ * square driver uses the modulus strategy).
+ *
+ *   batch            number of matrices, >= 0
+ *   m, n             HOST arrays of the shapes, 1 <= m, n <= 65536, min(m, n) <= 4096
+ *   aoffs            HOST array: A_i (m x n, column-major) starts at element aoffs[i] of A
+ *   uoffs, voffs     HOST arrays: U_i (m x k) and V_i (n x k), column-major, in U and V
+ *   soffs            HOST array: the k singular values of matrix i, descending, in S
+ *   sweeps, info     nullable device arrays (one int32 per matrix), as for k2svd_?kogbet;
+ *                    info -1 (NaN outputs) for a matrix with a non-finite element
+ *   flags            0 or K2SVD_KOG_NOTUNE
+ *   workspace        device scratch of ws_bytes bytes, 256-byte aligned, from
+ *                    k2svd_?gesvdr_ws for the same batch, m, n and flags; owned by the caller
+ * Argument order for error codes: 1 batch, 2 m, 3 n, 4 aoffs, 5 uoffs, 6 voffs, 7 soffs,
+ * 8 A, 9 U, 10 V, 11 S, 14 max_sweeps, 15 tol_factor, 16 flags, 17 workspace, 18 ws_bytes;
+ * -19 when the square driver rejects the reduced problem; K2SVD_ECUDA for CUDA errors.
+ */
+int k2svd_dgesvdr_ws(int64_t batch, const int32_t *m, const int32_t *n, int32_t flags, size_t *ws_bytes);
+int k2svd_sgesvdr_ws(int64_t batch, const int32_t *m, const int32_t *n, int32_t flags, size_t *ws_bytes);
+int k2svd_dgesvdr(int64_t batch, const int32_t *m, const int32_t *n, const int64_t *aoffs, const int64_t *uoffs,
+                  const int64_t *voffs, const int64_t *soffs, const double *A, double *U, double *V, double *S,
+                  int32_t *sweeps, int32_t *info, int32_t max_sweeps, double tol_factor, int32_t flags,
+                  void *workspace, size_t ws_bytes, void *stream);
+int k2svd_sgesvdr(int64_t batch, const int32_t *m, const int32_t *n, const int64_t *aoffs, const int64_t *uoffs,
+                  const int64_t *voffs, const int64_t *soffs, const float *A, float *U, float *V, float *S,
+                  int32_t *sweeps, int32_t *info, int32_t max_sweeps, double tol_factor, int32_t flags,
+                  void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * k2svd_zgesvd2 / k2svd_cgesvd2 -- SVD of `batch` complex 2x2 matrices (Sect. 3.4),
  * G = U diag(sigma1, sigma2) V^H with U, V unitary and sigma1 >= sigma2 >= 0.  A real G
  * (every imaginary part zero) gets the real method (k2svd_?gesvd2's results, imaginary parts

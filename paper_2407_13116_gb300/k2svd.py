@@ -8,6 +8,7 @@ the library has not been built (``python -c "import __graft_entry__ as g; g.buil
 import ctypes as C
 import os
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -49,6 +50,13 @@ def _bind_extra(L):
     L.k2svd_dgesvd2_bwd.restype = C.c_int
     L.k2svd_sgesvd2_bwd.argtypes = [I64, P, P, P, I64, P, P, P, P, F, P]
     L.k2svd_sgesvd2_bwd.restype = C.c_int
+    for p in ("d", "s"):
+        f = getattr(L, "k2svd_%sgesvdr_ws" % p)
+        f.argtypes = [I64, P, P, I32, C.POINTER(SZ)]
+        f.restype = C.c_int
+        f = getattr(L, "k2svd_%sgesvdr" % p)
+        f.argtypes = [I64, P, P, P, P, P, P, P, P, P, P, P, P, I32, D, I32, P, SZ, P]
+        f.restype = C.c_int
     for p in ("z", "c"):
         f = getattr(L, "k2svd_%sgesvd2" % p)
         f.argtypes = [I64, P, I64, P, I64, P, I64, P, I64, P, P]
@@ -171,6 +179,52 @@ def trsvd2(F, Gu, H, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_e
     if rc != 0:
         raise K2SVDError("k2svd_%strsvd2 returned %d" % (p, rc))
     return U, V, S, Se, Sf, info
+
+
+def rect_layout(shapes):
+    """Packed layout of a batch of m x n matrices: (m, n, aoffs, uoffs, voffs, soffs, sizes)
+    with A_i, U_i (m x k), V_i (n x k), S_i (k), k = min(m, n), consecutive and column-major;
+    sizes = (total A, total U, total V, total S)."""
+    shp = np.asarray(shapes, dtype=np.int64).reshape(-1, 2)
+    m, n = shp[:, 0], shp[:, 1]
+    k = np.minimum(m, n)
+    cum = lambda x: np.concatenate([[0], np.cumsum(x)[:-1]]).astype(np.int64)
+    return (m.astype(np.int32), n.astype(np.int32), cum(m * n), cum(m * k), cum(n * k), cum(k),
+            (int((m * n).sum()), int((m * k).sum()), int((n * k).sum()), int(k.sum())))
+
+
+def gesvdr(A, shapes, max_sweeps=40, tol_factor=1.0, flags=0):
+    """SVD of a packed batch of rectangular matrices (k2svd_?gesvdr): QR with column pivoting
+    to square, then the n x n Kogbetliantz driver.  A: flat tensor in rect_layout order.
+    Returns (U, S, V, sweeps, info), each flat in the same layout."""
+    p = _prefix(A.dtype)
+    dev = A.device
+    _check(A, "A", A.dtype, dev)
+    m, n, ao, uo, vo, so, (na, nu, nv, ns) = rect_layout(shapes)
+    if A.numel() < na:
+        raise K2SVDError("A holds %d elements, the shapes need %d" % (A.numel(), na))
+    b = len(m)
+    U = torch.empty(nu, dtype=A.dtype, device=dev)
+    V = torch.empty(nv, dtype=A.dtype, device=dev)
+    S = torch.empty(ns, dtype=A.dtype, device=dev)
+    sw = torch.empty(b, dtype=torch.int32, device=dev)
+    info = torch.empty(b, dtype=torch.int32, device=dev)
+    L = lib()
+    wsb = C.c_size_t(0)
+    rc = getattr(L, "k2svd_%sgesvdr_ws" % p)(b, m.ctypes.data, n.ctypes.data, int(flags), C.byref(wsb))
+    if rc != 0:
+        raise K2SVDError("k2svd_%sgesvdr_ws returned %d" % (p, rc))
+    ws = torch.empty(wsb.value + 256, dtype=torch.uint8, device=dev)
+    wp = (ws.data_ptr() + 255) // 256 * 256
+    with torch.cuda.device(dev):
+        rc = getattr(L, "k2svd_%sgesvdr" % p)(b, m.ctypes.data, n.ctypes.data, ao.ctypes.data, uo.ctypes.data,
+                                              vo.ctypes.data, so.ctypes.data, _ptr(A), _ptr(U), _ptr(V), _ptr(S),
+                                              _ptr(sw), _ptr(info), int(max_sweeps), float(tol_factor), int(flags),
+                                              C.c_void_p(wp), wsb.value, _stream())
+    if rc != 0:
+        raise K2SVDError("k2svd_%sgesvdr returned %d" % (p, rc))
+    torch.cuda.current_stream(dev).synchronize()      # the workspace is released on return
+    return U, S, V, sw, info
 
 
 def cgesvd2(G, U=None, V=None, S=None, want_info=True):
