@@ -52,9 +52,11 @@ def parse():
     p.add_argument("--no-phases", action="store_true")
     p.add_argument("--no-complex", action="store_true")
     p.add_argument("--no-rect", action="store_true")
-    p.add_argument("--profile-case", choices=["d", "s", "kog", "z"], default=None,
-                   help="run a small case of the 2x2 kernels (d, s), of the complex kernel (z) or "
-                        "of the persistent Kogbetliantz kernel (kog), for ncu captures, and exit")
+    p.add_argument("--no-ncr", action="store_true")
+    p.add_argument("--profile-case", choices=["d", "s", "dn", "sn", "kog", "z"], default=None,
+                   help="run a small case of the 2x2 kernels (d, s; dn, sn: the variant with the hypot "
+                        "that is not correctly rounded), of the complex kernel (z) or of the persistent "
+                        "Kogbetliantz kernel (kog), for ncu captures, and exit")
     p.add_argument("--profile-n", type=int, default=1 << 22)
     return p.parse_args()
 
@@ -162,9 +164,9 @@ class Clocks:
 # dram__bytes_write.sum) of `python bench.py --profile-case d` (2^22 matrices), scaled by
 # the matrix count to a full 2^27-matrix launch.  Valid only for the kernel sources with
 # this hash; any change to them reports null until a new capture is taken.
-TRAFFIC_SRC_HASH = "92a0114ef9e874a3"
-TRAFFIC_BYTES_PER_MATRIX = (134.417664e6 + 284.337664e6) / (1 << 22)
-KERNEL_SOURCES = ("k2_fp.cuh", "k2_svd2.cuh", "k2_gesvd2.cu")
+TRAFFIC_SRC_HASH = "94425b6fb0797ba1"
+TRAFFIC_BYTES_PER_MATRIX = (134.603008e6 + 284.823808e6) / (1 << 22)
+KERNEL_SOURCES = ("k2_fp.cuh", "k2_svd2.cuh", "k2_svd2_kernel.cuh", "k2_gesvd2.cu")
 
 
 def kernel_hash():
@@ -211,13 +213,15 @@ def slot_costs(c, rates, prec):
     A division and a square root cost rate(fma)/rate(div) and rate(fma)/rate(sqrt) fma
     slots of their pipe (measured); a correctly rounded hypot costs one multiplication,
     one fma and one square root; eq. (EXT) is integer work for double (0 FP slots) and a
-    double multiplication, fma and division for float."""
+    double multiplication, fma and division for float; the square roots of the variant's
+    hypot cost one square root each."""
+    sq = c.get("sqrt", 0.0)
     if prec == "d":
         wd, ws = rates["dfma"] / rates["ddiv"], rates["dfma"] / rates["dsqrt"]
-        fp64 = c["add"] + c["mul"] + c["fma"] + c["div"] * wd + c["hypot"] * (2 + ws)
+        fp64 = c["add"] + c["mul"] + c["fma"] + c["div"] * wd + c["hypot"] * (2 + ws) + sq * ws
         return {"fp64": fp64, "fp32": 0.0}
     wd, ws = rates["ffma"] / rates["fdiv"], rates["ffma"] / rates["fsqrt"]
-    fp32 = c["add"] + c["mul"] + c["fma"] + c["div"] * wd + c["hypot"] * (2 + ws)
+    fp32 = c["add"] + c["mul"] + c["fma"] + c["div"] * wd + c["hypot"] * (2 + ws) + sq * ws
     fp64 = c["ext"] * (2 + rates["dfma"] / rates["ddiv"])
     return {"fp64": fp64, "fp32": fp32}
 
@@ -239,8 +243,9 @@ def probe_rates(L):
 # ----------------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------------
-def leg(prec, n_half, steps, warmup, dev, D, clocks_index=None):
-    """Time `steps` steps of gesvd2(n_half general) + trsvd2(n_half triangular)."""
+def leg(prec, n_half, steps, warmup, dev, D, clocks_index=None, ncr=False):
+    """Time `steps` steps of gesvd2(n_half general) + trsvd2(n_half triangular) (ncr: the
+    variant with the hypot that is not correctly rounded)."""
     import torch
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
@@ -255,8 +260,8 @@ def leg(prec, n_half, steps, warmup, dev, D, clocks_index=None):
     torch.cuda.synchronize()
 
     def step():
-        k2svd.gesvd2(G, U=Ug, V=Vg, S=Sg, want_info=False)
-        k2svd.trsvd2(F, Gu, H, U=Ut, V=Vt, S=St, want_info=False)
+        k2svd.gesvd2(G, U=Ug, V=Vg, S=Sg, want_info=False, ncr=ncr)
+        k2svd.trsvd2(F, Gu, H, U=Ut, V=Vt, S=St, want_info=False, ncr=ncr)
 
     for _ in range(warmup):
         step()
@@ -273,9 +278,9 @@ def leg(prec, n_half, steps, warmup, dev, D, clocks_index=None):
     t0.record(stream)
     for k in range(steps):
         ev[k][0].record(stream)
-        k2svd.gesvd2(G, U=Ug, V=Vg, S=Sg, want_info=False)
+        k2svd.gesvd2(G, U=Ug, V=Vg, S=Sg, want_info=False, ncr=ncr)
         ev[k][1].record(stream)
-        k2svd.trsvd2(F, Gu, H, U=Ut, V=Vt, S=St, want_info=False)
+        k2svd.trsvd2(F, Gu, H, U=Ut, V=Vt, S=St, want_info=False, ncr=ncr)
         ev[k][2].record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
@@ -287,6 +292,34 @@ def leg(prec, n_half, steps, warmup, dev, D, clocks_index=None):
     del G, T3, F, Gu, H, Ug, Vg, Sg, Ut, Vt, St
     torch.cuda.empty_cache()
     return {"ms": ms, "ge_ms": ge_ms, "tr_ms": tr_ms, "clocks": clocks, "launches": 2 * steps}
+
+
+def ncr_leg(steps, warmup, dev, D, rates, clk_mhz, oc, value_cr, fp32_cr):
+    """The variant with the hypot that is not correctly rounded (Alg. 1's branch for it) on
+    the headline workloads: 2^27 + 2^27 FP64 and 2^28 + 2^28 FP32 wide-range matrices."""
+    out = {}
+    for prec, n_half, cr in (("d", N_HALF_D, value_cr), ("s", N_HALF_S, (fp32_cr or {}).get("value"))):
+        r = leg(prec, n_half, steps, warmup, dev, D, ncr=True)
+        ms = D.max(r["ms"])
+        v = D.world * 2 * n_half / (ms / 1e3)
+        c_ge = slot_costs(oc["wide_%s_gesvd2_ncr" % prec], rates, prec)
+        c_tr = slot_costs(oc["wide_%s_trsvd2_ncr" % prec], rates, prec)
+        o = {"value": v, "unit": "SVDs/s", "ms_per_step": ms, "gesvd2_ms": r["ge_ms"], "trsvd2_ms": r["tr_ms"],
+             "matrices_per_gpu_per_step": 2 * n_half,
+             "vs_correctly_rounded": (v / cr) if cr else None}
+        if prec == "d":
+            peak = fp64_peak(clk_mhz)
+            ach = n_half * c_ge["fp64"] / (r["ge_ms"] / 1e3)
+            o["roofline"] = {"bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9, "unit": "G FP64-pipe op/s",
+                             "frac": ach / peak, "kernel": "svd2_kernel<double,false,true> (k2svd_dgesvd2_ncr)",
+                             "ops_per_matrix": c_ge["fp64"]}
+        else:
+            roof32 = 2 / ((c_ge["fp32"] + c_tr["fp32"]) / rates["ffma"])
+            roof64 = 2 / ((c_ge["fp64"] + c_tr["fp64"]) / rates["dfma"])
+            o["frac_of_min_roofline"] = v / D.world / min(roof32, roof64)
+        out[prec] = o
+    out["workload"] = "the headline wide-range workloads through k2svd_{d,s}gesvd2_ncr / k2svd_{d,s}trsvd2_ncr"
+    return out
 
 
 def fwd_bwd_leg(steps, warmup, dev, D, rates, clk_mhz):
@@ -717,6 +750,8 @@ def run_ours(a):
                        "roofline_svds_per_s": {"fp32_pipe": roof32, "fp64_pipe": roof64, "hbm": roofhbm},
                        "frac_of_min_roofline": vs / D.world / min(roof32, roof64, roofhbm),
                        "gesvd2_ms": rs["ge_ms"], "trsvd2_ms": rs["tr_ms"]}
+    if not a.no_ncr:
+        out["ncr"] = ncr_leg(a.steps, a.warmup, dev, D, rates, clk_mhz, oc, value, out.get("fp32"))
     if not a.no_fwd_bwd:
         out["fwd_bwd"] = fwd_bwd_leg(a.steps, a.warmup, dev, D, rates, clk_mhz)
     if not a.no_phases:
@@ -805,12 +840,13 @@ def profile_case(a):
               (len(orders), sw.double().mean().item(), int((info == 0).sum().item())))
         return
     n = a.profile_n
-    G = I.general(n, SEED + 2, a.profile_case, "wide", xp="torch", device=dev)
-    T3 = I.triangular(n, SEED + 3, a.profile_case, "wide", xp="torch", device=dev)
+    prec, ncr = a.profile_case[0], a.profile_case.endswith("n")
+    G = I.general(n, SEED + 2, prec, "wide", xp="torch", device=dev)
+    T3 = I.triangular(n, SEED + 3, prec, "wide", xp="torch", device=dev)
     torch.cuda.synchronize()
     for _ in range(3):
-        k2svd.gesvd2(G, want_info=False)
-        k2svd.trsvd2(T3[0], T3[1], T3[2], want_info=False)
+        k2svd.gesvd2(G, want_info=False, ncr=ncr)
+        k2svd.trsvd2(T3[0], T3[1], T3[2], want_info=False, ncr=ncr)
     torch.cuda.synchronize()
     print("profile case %s n=%d done" % (a.profile_case, n))
 

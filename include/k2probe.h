@@ -28,12 +28,19 @@ int k2probe_rate(int op, double *rate);
  * device arrays of n doubles: q[i] = a[i] / b[i] by the integer-pipe correctly rounded
  * division, h[i] = hypot(a[i], b[i]) by the correctly rounded hypot (Sect. 2).  For testing
  * these primitives against the FP64 divider and an exact reference; not part of the method.
- * Returns 0, -1 (n < 0 or a CUDA error), -2 (null pointer).  Asynchronous on `stream`.
+ * Returns 0, -1 (n < 0), -2 (null pointer), -1000 (a CUDA launch error).  Asynchronous on
+ * `stream`.
  */
 int k2probe_div(int64_t n, const double *a, const double *b, double *q, void *stream);
 int k2probe_hypot(int64_t n, const double *a, const double *b, double *h, void *stream);
 /* k2probe_hypotf -- the binary32 correctly rounded hypot, same conventions. */
 int k2probe_hypotf(int64_t n, const float *a, const float *b, float *h, void *stream);
+/* k2probe_hypot_ncr / k2probe_hypotf_ncr -- the hypot that is not correctly rounded, used by
+ * the k2svd_?gesvd2_ncr variant (Alg. 1's branch for such a hypot): xLAPY2's scaled formula
+ * w * sqrt(fma(q, q, 1)), q = z / w, w = max(|a|,|b|), z = min(|a|,|b|), each step rounded to
+ * nearest; +Inf if an argument is infinite, else NaN if one is NaN.  Same conventions. */
+int k2probe_hypot_ncr(int64_t n, const double *a, const double *b, double *h, void *stream);
+int k2probe_hypotf_ncr(int64_t n, const float *a, const float *b, float *h, void *stream);
 
 #ifdef __cplusplus
 }

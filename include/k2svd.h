@@ -50,6 +50,8 @@ extern "C" {
 #define K2SVD_INFO_T2INF    (1 << 13)  /* tan(2 phi) = inf, tan(phi) = 1 (Alg. 1)              */
 #define K2SVD_INFO_TPINF    (1 << 14)  /* tan(psi) = inf, eq. (tp') (Alg. 2)                   */
 #define K2SVD_INFO_PSIG     (1 << 15)  /* singular values reordered by eq. (prec) (Alg. 2)     */
+#define K2SVD_INFO_T2NCR    (1 << 18)  /* tan(2 phi) by Alg. 1's branch for a hypot that is not
+                                          correctly rounded (the k2svd_?gesvd2_ncr variant only) */
 
 /*
  * k2svd_dgesvd2 / k2svd_sgesvd2 -- SVD of `batch` general real 2x2 matrices.
@@ -98,6 +100,36 @@ int k2svd_strsvd2(int64_t batch, const float *F, const float *Gu, const float *H
                   float *U, int64_t ldu, float *V, int64_t ldv,
                   float *S, int64_t lds, int32_t *Se, float *Sf,
                   int32_t *info, void *stream);
+
+/*
+ * k2svd_dgesvd2_ncr / k2svd_sgesvd2_ncr, k2svd_dtrsvd2_ncr / k2svd_strsvd2_ncr -- the same
+ * SVDs with a hypot that is not correctly rounded, the case for which Alg. 1 (Sect. 3.3.1)
+ * has its own branch: after the three special cases of Alg. 1, tan(2 phi) comes from
+ * x = r12/r11, y = r22/r11 (r11 > r12) or x = r11/r12, y = r22/r12 (otherwise) as
+ * fl(fl(2x)y) or 2y divided by max(fma(x - y, x + y, 1), 0), without squaring; and every
+ * hypot of the method (Alg. 1, Alg. 2, Sect. 3.1, Sect. 3.2.2) is xLAPY2's scaled formula
+ * w * sqrt(fma(q, q, 1)), q = z / w, w = max(|x|,|y|), z = min(|x|,|y|), each step rounded to
+ * nearest (at most 3.5 units of 2^-p from the exact value).  The paper gives no relative
+ * error bound for this variant.  Arguments, layout, ownership, error codes and the handling
+ * of non-finite inputs are those of k2svd_?gesvd2 and k2svd_?trsvd2; info carries
+ * K2SVD_INFO_T2NCR where the branch ran.
+ */
+int k2svd_dgesvd2_ncr(int64_t batch, const double *G, int64_t ldg,
+                      double *U, int64_t ldu, double *V, int64_t ldv,
+                      double *S, int64_t lds, int32_t *Se, double *Sf,
+                      int32_t *info, void *stream);
+int k2svd_sgesvd2_ncr(int64_t batch, const float *G, int64_t ldg,
+                      float *U, int64_t ldu, float *V, int64_t ldv,
+                      float *S, int64_t lds, int32_t *Se, float *Sf,
+                      int32_t *info, void *stream);
+int k2svd_dtrsvd2_ncr(int64_t batch, const double *F, const double *Gu, const double *H,
+                      double *U, int64_t ldu, double *V, int64_t ldv,
+                      double *S, int64_t lds, int32_t *Se, double *Sf,
+                      int32_t *info, void *stream);
+int k2svd_strsvd2_ncr(int64_t batch, const float *F, const float *Gu, const float *H,
+                      float *U, int64_t ldu, float *V, int64_t ldv,
+                      float *S, int64_t lds, int32_t *Se, float *Sf,
+                      int32_t *info, void *stream);
 
 /*
  * k2svd_dgesvdr_ws / k2svd_sgesvdr_ws, k2svd_dgesvdr / k2svd_sgesvdr -- SVD of `batch`

@@ -34,6 +34,7 @@
 #define K2REF_F_T2INF    0x20  /* tan(2phi) infinite, tan(phi) = 1 (Alg. 1)     */
 #define K2REF_F_TPINF    0x40  /* tan(psi) infinite, eq. (tp') (Alg. 2)         */
 #define K2REF_F_PSIG     0x80  /* singular values swapped by eq. (prec)         */
+#define K2REF_F_T2NCR    0x400 /* tan(2phi) by Alg. 1's branch for a hypot that is not correctly rounded */
 
 /* ------------------------------------------------------------------------- */
 /* Unsigned big integers, little-endian base-2^32 limbs: exact squares and    */
@@ -107,10 +108,10 @@ static int bn_cmp(const bn_t *a, const bn_t *b)
 }
 
 /* Operation counters (per thread) for the algorithmic operation count of the method:
- * additions/subtractions, multiplications, fmas, divisions, correctly rounded hypots and
- * evaluations of eq. (EXT).  Exact power-of-two scalings, comparisons and sign changes
- * are not counted. */
-enum { OP_ADD, OP_MUL, OP_FMA, OP_DIV, OP_HYP, OP_EXT, OP_N };
+ * additions/subtractions, multiplications, fmas, divisions, correctly rounded hypots,
+ * evaluations of eq. (EXT) and square roots (those of the hypot that is not correctly
+ * rounded).  Exact power-of-two scalings, comparisons and sign changes are not counted. */
+enum { OP_ADD, OP_MUL, OP_FMA, OP_DIV, OP_HYP, OP_EXT, OP_SQRT, OP_N };
 static _Thread_local long long k2ref_ops_d[OP_N], k2ref_ops_s[OP_N];
 #define K2OP(k) ((void)(SFX(k2ref_ops)[k]++))
 
@@ -134,6 +135,7 @@ static _Thread_local long long k2ref_ops_d[OP_N], k2ref_ops_s[OP_N];
 #define FREXP frexp
 #define LDEXP ldexp
 #define WSQRT sqrtf128
+#define RSQRT sqrt
 #define RBITS uint64_t
 #include "k2ref_body.inc"
 #undef R
@@ -153,6 +155,7 @@ static _Thread_local long long k2ref_ops_d[OP_N], k2ref_ops_s[OP_N];
 #undef FREXP
 #undef LDEXP
 #undef WSQRT
+#undef RSQRT
 #undef RBITS
 
 /* ------------------------------------------------------------------------- */
@@ -175,11 +178,12 @@ static _Thread_local long long k2ref_ops_d[OP_N], k2ref_ops_s[OP_N];
 #define FREXP frexpf
 #define LDEXP ldexpf
 #define WSQRT sqrt
+#define RSQRT sqrtf
 #define RBITS uint32_t
 #include "k2ref_body.inc"
 
 /* Read (and optionally reset) the calling thread's operation counters. */
-void k2ref_opcount(int prec_double, long long out[6], int reset)
+void k2ref_opcount(int prec_double, long long out[7], int reset)
 {
     long long *c = prec_double ? k2ref_ops_d : k2ref_ops_s;
     for (int k = 0; k < OP_N; ++k) { out[k] = c[k]; if (reset) c[k] = 0; }

@@ -20,7 +20,7 @@ _lib = None
 
 # Branch flags of info bits 8..15 (see k2ref.c)
 FLAGS = {"ext": 0x01, "fallback": 0x02, "swap": 0x04, "t2f2": 0x08, "t2f3": 0x10,
-         "t2inf": 0x20, "tpinf": 0x40, "psig": 0x80}
+         "t2inf": 0x20, "tpinf": 0x40, "psig": 0x80, "t2ncr": 0x400}
 
 
 def _sources():
@@ -57,13 +57,20 @@ def lib():
             L = C.CDLL(_SO)
             P, I64, I32, D, F = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_float
             for sfx in ("d", "s"):
-                fn = getattr(L, "k2ref_gesvd2_" + sfx)
-                fn.argtypes = [I64, P, I64, P, I64, P, I64, P, I64, P, P, P, C.c_int]
-                fn.restype = C.c_int
-                fn = getattr(L, "k2ref_trsvd2_" + sfx)
-                fn.argtypes = [I64, P, P, P, P, I64, P, I64, P, I64, P, P, P, C.c_int]
-                fn.restype = C.c_int
+                for nm in ("k2ref_gesvd2_", "k2ref_gesvd2_ncr_"):
+                    fn = getattr(L, nm + sfx)
+                    fn.argtypes = [I64, P, I64, P, I64, P, I64, P, I64, P, P, P, C.c_int]
+                    fn.restype = C.c_int
+                for nm in ("k2ref_trsvd2_", "k2ref_trsvd2_ncr_"):
+                    fn = getattr(L, nm + sfx)
+                    fn.argtypes = [I64, P, P, P, P, I64, P, I64, P, I64, P, P, P, C.c_int]
+                    fn.restype = C.c_int
                 T = D if sfx == "d" else F
+                fn = getattr(L, "k2ref_hypot_ncr_" + sfx)
+                fn.argtypes = [T, T]
+                fn.restype = T
+                getattr(L, "k2ref_hypot_ncr_n_" + sfx).argtypes = [I64, P, P, P, C.c_int]
+                getattr(L, "k2ref_trace_m_" + sfx).argtypes = [P, P, P, C.c_int]
                 fn = getattr(L, "k2ref_hypot_" + sfx)
                 fn.argtypes = [T, T]
                 getattr(L, "k2ref_hypot_n_" + sfx).argtypes = [I64, P, P, P, C.c_int]
@@ -111,32 +118,33 @@ def _dt(prec):
     return np.float64 if prec == "d" else np.float32
 
 
-def gesvd2(G, prec="d", nthreads=1):
+def gesvd2(G, prec="d", nthreads=1, ncr=False):
     """SVD of a batch of 2x2 matrices given as SoA planes G[4, n] (g11, g21, g12, g22).
 
     Returns a dict with U[4,n], V[4,n] (column-major planes), S[2,n] (rounded singular
-    values), Se[2,n] and Sf[2,n] (exact (e,f) form) and info[n]."""
+    values), Se[2,n] and Sf[2,n] (exact (e,f) form) and info[n].  ncr: the method with the
+    hypot that is not correctly rounded (xLAPY2's formula) and Alg. 1's branch for it."""
     T = _dt(prec)
     G = np.ascontiguousarray(G, dtype=T)
     n = G.shape[1]
     U = np.empty((4, n), T); V = np.empty((4, n), T); S = np.empty((2, n), T)
     Se = np.empty((2, n), np.int32); Sf = np.empty((2, n), T); info = np.empty(n, np.int32)
-    rc = getattr(lib(), "k2ref_gesvd2_" + prec)(n, _ptr(G), n, _ptr(U), n, _ptr(V), n, _ptr(S), n,
+    rc = getattr(lib(), ("k2ref_gesvd2_ncr_" if ncr else "k2ref_gesvd2_") + prec)(n, _ptr(G), n, _ptr(U), n, _ptr(V), n, _ptr(S), n,
                                                  _ptr(Se), _ptr(Sf), _ptr(info), int(nthreads))
     if rc != 0:
         raise ValueError("k2ref_gesvd2 returned %d" % rc)
     return {"U": U, "V": V, "S": S, "Se": Se, "Sf": Sf, "info": info}
 
 
-def trsvd2(F, Gp, H, prec="d", nthreads=1):
-    """SVD of upper-triangular R = [[F, Gp], [0, H]] given as three planes."""
+def trsvd2(F, Gp, H, prec="d", nthreads=1, ncr=False):
+    """SVD of upper-triangular R = [[F, Gp], [0, H]] given as three planes (ncr: as gesvd2)."""
     T = _dt(prec)
     F = np.ascontiguousarray(F, dtype=T); Gp = np.ascontiguousarray(Gp, dtype=T)
     H = np.ascontiguousarray(H, dtype=T)
     n = F.shape[0]
     U = np.empty((4, n), T); V = np.empty((4, n), T); S = np.empty((2, n), T)
     Se = np.empty((2, n), np.int32); Sf = np.empty((2, n), T); info = np.empty(n, np.int32)
-    rc = getattr(lib(), "k2ref_trsvd2_" + prec)(n, _ptr(F), _ptr(Gp), _ptr(H), _ptr(U), n, _ptr(V), n,
+    rc = getattr(lib(), ("k2ref_trsvd2_ncr_" if ncr else "k2ref_trsvd2_") + prec)(n, _ptr(F), _ptr(Gp), _ptr(H), _ptr(U), n, _ptr(V), n,
                                                  _ptr(S), n, _ptr(Se), _ptr(Sf), _ptr(info), int(nthreads))
     if rc != 0:
         raise ValueError("k2ref_trsvd2 returned %d" % rc)
@@ -154,6 +162,20 @@ def hypot_n(x, y, prec="d", nthreads=1):
     x = np.ascontiguousarray(x, dtype=T); y = np.ascontiguousarray(y, dtype=T)
     h = np.empty_like(x)
     getattr(lib(), "k2ref_hypot_n_" + prec)(x.size, _ptr(x), _ptr(y), _ptr(h), int(nthreads))
+    return h
+
+
+def hypot_ncr(x, y, prec="d"):
+    """The hypot that is not correctly rounded (xLAPY2's scaled formula, every step rounded once)."""
+    return getattr(lib(), "k2ref_hypot_ncr_" + prec)(x, y)
+
+
+def hypot_ncr_n(x, y, prec="d", nthreads=1):
+    """hypot_ncr of arrays x, y, elementwise."""
+    T = _dt(prec)
+    x = np.ascontiguousarray(x, dtype=T); y = np.ascontiguousarray(y, dtype=T)
+    h = np.empty_like(x)
+    getattr(lib(), "k2ref_hypot_ncr_n_" + prec)(x.size, _ptr(x), _ptr(y), _ptr(h), int(nthreads))
     return h
 
 
@@ -199,12 +221,12 @@ def cgesvd2(G, prec="d", nthreads=1):
     return U, V, S, info
 
 
-def trace(g, prec="d"):
+def trace(g, prec="d", ncr=False):
     """Intermediate values of one SVD: (r11, r12, r22, tan2phi, tanphi, tanpsi, tantheta), (t, t', s, flags)."""
     T = _dt(prec)
     g = np.ascontiguousarray(g, dtype=T)
     tr = np.zeros(7, T); ints = np.zeros(4, np.int32)
-    getattr(lib(), "k2ref_trace_" + prec)(_ptr(g), _ptr(tr), _ptr(ints))
+    getattr(lib(), "k2ref_trace_m_" + prec)(_ptr(g), _ptr(tr), _ptr(ints), int(bool(ncr)))
     return tr, ints
 
 
@@ -229,24 +251,25 @@ def ext(x1, y1, x2, y2, neg, d, sec, prec="d"):
     return getattr(lib(), "k2ref_ext_" + prec)(x1, y1, x2, y2, int(neg), d, sec)
 
 
-OPS = ("add", "mul", "fma", "div", "hypot", "ext")
+OPS = ("add", "mul", "fma", "div", "hypot", "ext", "sqrt")
 
 
-def opcount(G, prec="d", triangular=False, complex_planes=False):
+def opcount(G, prec="d", triangular=False, complex_planes=False, ncr=False):
     """Mean algorithmic operation counts per matrix of the method on a batch (one thread):
-    {add, mul, fma, div, hypot, ext} (exact scalings, comparisons and sign changes excluded).
-    complex_planes: G is 8 planes of complex matrices (Sect. 3.4)."""
+    {add, mul, fma, div, hypot, ext, sqrt} (exact scalings, comparisons and sign changes
+    excluded; sqrt counts the square roots of the hypot that is not correctly rounded).
+    complex_planes: G is 8 planes of complex matrices (Sect. 3.4); ncr: see gesvd2."""
     L = lib()
-    buf = np.zeros(6, np.int64)
+    buf = np.zeros(7, np.int64)
     L.k2ref_opcount(1 if prec == "d" else 0, _ptr(buf), 1)
     if complex_planes:
         cgesvd2(G, prec, nthreads=1)
         n = G.shape[1]
     elif triangular:
-        trsvd2(G[0], G[1], G[2], prec, nthreads=1)
+        trsvd2(G[0], G[1], G[2], prec, nthreads=1, ncr=ncr)
         n = G.shape[1]
     else:
-        gesvd2(G, prec, nthreads=1)
+        gesvd2(G, prec, nthreads=1, ncr=ncr)
         n = G.shape[1]
     L.k2ref_opcount(1 if prec == "d" else 0, _ptr(buf), 1)
     return {k: float(v) / n for k, v in zip(OPS, buf)}

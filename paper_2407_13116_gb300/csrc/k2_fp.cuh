@@ -473,6 +473,41 @@ __device__ __forceinline__ float hypot_cr_body(float x, float y)
 static __device__ __noinline__ float hypot_cr(float x, float y) { return hypot_cr_body(x, y); }
 
 // ---------------------------------------------------------------------------------------
+// A hypot that is not correctly rounded, for Alg. 1's branch for that case: the scaled
+// formula of LAPACK's xLAPY2, w sqrt(1 + (z/w)^2) with w = max(|x|,|y|), z = min(|x|,|y|),
+// each step one IEEE rounding to nearest: q = z/w, r = fma(q, q, 1), w * sqrt(r).  The
+// steps neither overflow nor underflow (q <= 1, 1 <= r <= 2); only the last product may
+// overflow, to infinity.  Relative error below 3.5 u, u = 2^-p, to first order: the
+// rounding of q changes sqrt(1 + q^2) by at most u, that of r by u/2, the root's and the
+// product's by u each.  The quotient is the method's division; the square root is the
+// FP64 (FP32) pipe's.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double hypot_ncr_body(double x, double y)
+{
+    double a = absv(x), b = absv(y);
+    if (is_inf(a) || is_inf(b)) return dfrom(0x7FFull << 52);
+    if (!is_fin(a) || !is_fin(b)) return dfrom(0x7FF8000000000000ull);
+    if (pos_lt(a, b)) { const double t = a; a = b; b = t; }
+    if (eq0(b)) return a;
+    const double q = div_rn(b, a);
+    return __dmul_rn(a, __dsqrt_rn(__fma_rn(q, q, 1.0)));
+}
+static __device__ __noinline__ uint64_t hypot_ncr_bits(uint64_t x, uint64_t y) { return dbits(hypot_ncr_body(dfrom(x), dfrom(y))); }
+__device__ __forceinline__ double hypot_ncr(double x, double y) { return dfrom(hypot_ncr_bits(dbits(x), dbits(y))); }
+
+__device__ __forceinline__ float hypot_ncr_body(float x, float y)
+{
+    float a = fabsf(x), b = fabsf(y);
+    if (is_inf(a) || is_inf(b)) return ffrom(0xFFu << 23);
+    if (!is_fin(a) || !is_fin(b)) return ffrom(0x7FC00000u);
+    if (a < b) { const float t = a; a = b; b = t; }
+    if (b == 0.0f) return a;
+    const float q = __fdiv_rn(b, a);
+    return __fmul_rn(a, __fsqrt_rn(__fmaf_rn(q, q, 1.0f)));
+}
+static __device__ __noinline__ float hypot_ncr(float x, float y) { return hypot_ncr_body(x, y); }
+
+// ---------------------------------------------------------------------------------------
 // eq. (EXT) for double: fl(FL(FL(x1 y1 +- x2 y2) / d)) with FL = IEEE binary128 rounding
 // (113 bits, ties to even) and fl = binary64 rounding with gradual underflow, emulated
 // exactly in integers.  The caller then divides by sec(theta) in double.  All operands

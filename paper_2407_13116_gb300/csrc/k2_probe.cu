@@ -113,6 +113,38 @@ extern "C" int k2probe_hypot(int64_t n, const double *a, const double *b, double
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1000;
 }
 
+__global__ void hypot_ncr_kernel(int64_t n, const double *a, const double *b, double *h)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        h[i] = k2::hypot_ncr(a[i], b[i]);
+}
+
+__global__ void hypotf_ncr_kernel(int64_t n, const float *a, const float *b, float *h)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        h[i] = k2::hypot_ncr(a[i], b[i]);
+}
+
+extern "C" int k2probe_hypot_ncr(int64_t n, const double *a, const double *b, double *h, void *stream)
+{
+    if (n < 0) return -1;
+    if (n == 0) return 0;
+    if (!a || !b || !h) return -2;
+    int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    hypot_ncr_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, a, b, h);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1000;
+}
+
+extern "C" int k2probe_hypotf_ncr(int64_t n, const float *a, const float *b, float *h, void *stream)
+{
+    if (n < 0) return -1;
+    if (n == 0) return 0;
+    if (!a || !b || !h) return -2;
+    int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    hypotf_ncr_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, a, b, h);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1000;
+}
+
 extern "C" int k2probe_rate(int op, double *rate)
 {
     switch (op) {

@@ -19,6 +19,8 @@
 //  * (cos, sin) of phi +- theta follow the direction of (D, N) with N, D the numerator and
 //    denominator of eq. (tan+-); a zero D or an overflowing N/D gives (0, sign N); the bold
 //    phi with an infinite tangent (tan psi = 0 after the swap) gives pi/2 +- theta exactly.
+// With NCR = true (a separate variant) Alg. 1 takes its branch for a hypot that is not
+// correctly rounded, and every hypot of the method is xLAPY2's scaled formula (hypot_ncr).
 #pragma once
 #include "k2_fp.cuh"
 
@@ -26,7 +28,8 @@ namespace k2 {
 
 enum : int {
     FL_EXT = 0x01, FL_FALLBACK = 0x02, FL_SWAP = 0x04, FL_T2F2 = 0x08,
-    FL_T2F3 = 0x10, FL_T2INF = 0x20, FL_TPINF = 0x40, FL_PSIG = 0x80
+    FL_T2F3 = 0x10, FL_T2INF = 0x20, FL_TPINF = 0x40, FL_PSIG = 0x80,
+    FL_T2NCR = 0x400
 };
 
 // class of each zero-pattern type, eq. (ts): 9, 3, 5, 13 or 15
@@ -77,10 +80,18 @@ template <typename T> struct svd2_out {
     int info;
 };
 
-// sec = hypot(tan,1), cos = 1/sec, sin = tan/sec (Cor. 2.3, Lemma 3.2)
-template <typename T> __device__ __forceinline__ void cos_sin(T tn, T &c, T &s)
+// The method's hypot: correctly rounded (the paper's choice), or with NCR the scaled formula
+// that is not, the case for which Alg. 1 has its own branch.
+template <bool NCR, typename T> __device__ __forceinline__ T hyp(T x, T y)
 {
-    T sec = hypot_cr(tn, T(1));
+    if (NCR) return hypot_ncr(x, y);
+    return hypot_cr(x, y);
+}
+
+// sec = hypot(tan,1), cos = 1/sec, sin = tan/sec (Cor. 2.3, Lemma 3.2)
+template <bool NCR = false, typename T> __device__ __forceinline__ void cos_sin(T tn, T &c, T &s)
+{
+    T sec = hyp<NCR>(tn, T(1));
     c = qdiv(T(1), sec);
     s = qdiv(tn, sec);
 }
@@ -114,7 +125,7 @@ __device__ __forceinline__ void simple9(int tt, T g11, T g21, T g12, T g22, m22<
 }
 
 // Sect. 3.1, classes 3 (one non-zero column) and 5 (one non-zero row): one Givens rotation
-template <typename T>
+template <typename T, bool NCR = false>
 __device__ __forceinline__ void simple35(int tt, T g11, T g21, T g12, T g22, m22<T> &U, m22<T> &V, T &d1)
 {
     bool col = (tt == 3 || tt == 12);
@@ -127,8 +138,8 @@ __device__ __forceinline__ void simple35(int tt, T g11, T g21, T g12, T g22, m22
     bool p1 = pos_lt(y0, y1);
     T x = p1 ? y1 : y0, y = p1 ? y0 : y1;
     T c, s;
-    cos_sin(qdiv(y, x), c, s);
-    d1 = hypot_cr(x, y);
+    cos_sin<NCR>(qdiv(y, x), c, s);
+    d1 = hyp<NCR>(x, y);
     m22<T> R = rot(c, s);            // U_theta (column case) or V_theta (row case)
     if (p1) swap_rows(R);
     if (n0) neg_row(R, 0);
@@ -149,8 +160,9 @@ template <typename T> struct tri_out {
 // FP64 pipe has room: general matrices), else as every other division.  Same results.
 template <bool FDIV, typename T> __device__ __forceinline__ T csdiv(T a, T b) { return FDIV ? a / b : qdiv(a, b); }
 
-// Alg. 1 and Alg. 2 on R = [[r11, r12], [0, r22]] (all > 0), with the transpose-swap of eq. (RT)
-template <typename T, bool FDIV = false>
+// Alg. 1 and Alg. 2 on R = [[r11, r12], [0, r22]] (all > 0), with the transpose-swap of eq. (RT).
+// NCR: the hypot that is not correctly rounded, and Alg. 1's branch for it.
+template <typename T, bool FDIV = false, bool NCR = false>
 __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int &flags)
 {
     z.swap = pos_lt(r11, r22);
@@ -168,6 +180,14 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
     } else if (pos_lt(qdiv(ra, rb), fpt<T>::eps())) {                 // eq. (t2f''), only for t' ~ 13
         t2 = qdiv(T(2) * rc, rb);
         flags |= FL_T2F2;
+    } else if (NCR) {                                      // Alg. 1: tan(2 phi) without squaring
+        T x, y, num;
+        if (pos_lt(rb, ra)) { x = qdiv(rb, ra); y = qdiv(rc, ra); num = (T(2) * x) * y; }
+        else { x = qdiv(ra, rb); y = qdiv(rc, rb); num = T(2) * y; }
+        T den = fma(x - y, x + y, T(1));
+        if (!gt0(den)) den = T(0);                         // max(den, 0), -0 -> +0
+        t2 = qdiv(num, den);
+        flags |= FL_T2NCR;
     } else {                                               // eq. (t2f')
         T h = hypot_cr(ra, rb);
         if (pos_eq(h, rc)) { t2 = T(0); t2inf = true; }
@@ -179,8 +199,8 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
     if (is_inf(t2)) t2inf = true;
     T tf;
     if (t2inf) { tf = T(1); flags |= FL_T2INF; }
-    else tf = qdiv(t2, T(1) + hypot_cr(t2, T(1)));           // eq. (tf)
-    T secf = hypot_cr(tf, T(1));
+    else tf = qdiv(t2, T(1) + hyp<NCR>(t2, T(1)));           // eq. (tf)
+    T secf = hyp<NCR>(tf, T(1));
     z.tanphi = tf;
     z.cphi = csdiv<FDIV>(T(1), secf);
     z.sphi = csdiv<FDIV>(tf, secf);
@@ -197,7 +217,7 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
         s2 = ef_mul(erc, ecos);
         flags |= FL_TPINF;
     } else {                                               // eq. (s')
-        T secp = hypot_cr(tp, T(1));
+        T secp = hyp<NCR>(tp, T(1));
         z.cpsi = csdiv<FDIV>(T(1), secp);
         z.spsi = csdiv<FDIV>(tp, secp);
         ef<T> sf = ef_div(ef_of(secf), ef_of(secp));
@@ -251,8 +271,8 @@ __device__ __forceinline__ void phase1(T &g11, T &g21, T &g12, T &g22, int extra
     tp = !eq0(g11) | (!eq0(g21) << 1) | (!eq0(g12) << 2) | (!eq0(g22) << 3);
 }
 
-// FDIV: see csdiv; the results do not depend on it.
-template <typename T, bool FDIV = false>
+// FDIV: see csdiv; the results do not depend on it.  NCR: see tri_svd.
+template <typename T, bool FDIV = false, bool NCR = false>
 __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
 {
     int t, s, tp, flags = 0;
@@ -264,7 +284,7 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
     if (clsp == 9) {
         simple9(tp, g11, g21, g12, g22, o.U, o.V, d1, d2);
     } else if (clsp == 3 || clsp == 5) {
-        simple35(tp, g11, g21, g12, g22, o.U, o.V, d1);
+        simple35<T, NCR>(tp, g11, g21, g12, g22, o.U, o.V, d1);
     } else if (clsp == 13) {
         // Sect. 3.2.1: permute to upper triangular, signs of row 1, column 2, row 2
         simple = false;
@@ -278,7 +298,7 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
         bool n12 = lt0(b); b = absv(b); if (n12) d = ngt(d);
         bool n22 = lt0(d); d = absv(d);
         tri_out<T> z;
-        tri_svd<T, FDIV>(a, b, d, z, flags);
+        tri_svd<T, FDIV, NCR>(a, b, d, z, flags);
         m22<T> U = ucheck(z);                              // U = P_U S11 S22 U-check
         if (n11) neg_row(U, 0);
         if (n22) neg_row(U, 1);
@@ -289,7 +309,7 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
         o.U = U; o.V = V; o.s1 = z.s1; o.s2 = z.s2;
     } else {
         // Sect. 3.2.2: fully pivoted URV of a matrix without zeros
-        T w1 = hypot_cr(g11, g21), w2 = hypot_cr(g12, g22);
+        T w1 = hyp<NCR>(g11, g21), w2 = hyp<NCR>(g12, g22);
         bool pv = pos_lt(w1, w2);
         if (pv) { T x = g11; g11 = g12; g12 = x; x = g21; g21 = g22; g22 = x; w1 = w2; }
         bool n1a = lt0(g11), n1b = lt0(g21);            // S1
@@ -299,7 +319,7 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
         if (pu) { T x = g11; g11 = g21; g21 = x; x = g12; g12 = g22; g22 = x; }
         // eq. (QR15)
         const T tth = qdiv(g21, g11);
-        const T secth = hypot_cr(tth, T(1));
+        const T secth = hyp<NCR>(tth, T(1));
         T r11 = w1, r12, r22;
         if (eq0(fma(tth, g11, ngt(g21)))) {                // tan(theta) exact: Lemma 3.4
             r12 = qdiv(fma(g22, tth, g12), secth);
@@ -321,7 +341,7 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
             if (eq0(r12)) {
                 simple9<T>(!eq0(r22) ? 9 : 1, r11, T(0), T(0), r22, Ur, Vr, d1, d2);
             } else {
-                simple35<T>(5, r11, T(0), r12, T(0), Ur, Vr, d1);
+                simple35<T, NCR>(5, r11, T(0), r12, T(0), Ur, Vr, d1);
                 d2 = T(0);
             }
             // U_theta Ur, with Ur a signed permutation: pick and negate columns of U_theta
@@ -345,7 +365,7 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
             bool n22 = lt0(r22);
             if (n22) r22 = ngt(r22);                           // S22 R'
             tri_out<T> z;
-            tri_svd<T, FDIV>(r11, r12, r22, z, flags);
+            tri_svd<T, FDIV, NCR>(r11, r12, r22, z, flags);
             m22<T> V = vcheck(z);                          // V = P_V S12 V-check
             if (n12) neg_row(V, 1);
             if (pv) swap_rows(V);
@@ -366,7 +386,7 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
                     if (is_inf(ta)) { ca = T(0); sa = lt0(N) ? T(-1) : T(1); }
                     else {
                         T c0, s0;
-                        cos_sin(ta, c0, s0);
+                        cos_sin<NCR>(ta, c0, s0);
                         if (lt0(D)) { ca = ngt(c0); sa = ngt(s0); } else { ca = c0; sa = s0; }
                     }
                 }

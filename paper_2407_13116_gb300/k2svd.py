@@ -33,12 +33,13 @@ def lib():
         L = C.CDLL(path)
         P, I64 = C.c_void_p, C.c_int64
         for p in ("d", "s"):
-            f = getattr(L, "k2svd_%sgesvd2" % p)
-            f.argtypes = [I64, P, I64, P, I64, P, I64, P, I64, P, P, P, P]
-            f.restype = C.c_int
-            f = getattr(L, "k2svd_%strsvd2" % p)
-            f.argtypes = [I64, P, P, P, P, I64, P, I64, P, I64, P, P, P, P]
-            f.restype = C.c_int
+            for sfx in ("", "_ncr"):
+                f = getattr(L, "k2svd_%sgesvd2%s" % (p, sfx))
+                f.argtypes = [I64, P, I64, P, I64, P, I64, P, I64, P, P, P, P]
+                f.restype = C.c_int
+                f = getattr(L, "k2svd_%strsvd2%s" % (p, sfx))
+                f.argtypes = [I64, P, P, P, P, I64, P, I64, P, I64, P, P, P, P]
+                f.restype = C.c_int
         _bind_extra(L)
         _lib = L
     return _lib
@@ -114,11 +115,12 @@ def _planes(t, k, name):
     return t.stride(0) if t.shape[0] > 1 else t.shape[1]
 
 
-def gesvd2(G, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_ef=False, want_info=True):
+def gesvd2(G, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_ef=False, want_info=True, ncr=False):
     """SVD of the 2x2 matrices in the SoA planes G (4, n): (g11, g21, g12, g22).
 
     Returns (U, V, S, Se, Sf, info) with U, V (4, n) column-major planes, S (2, n) rounded
-    singular values, Se/Sf (2, n) the exact (e,f) form (None unless requested) and info (n,)."""
+    singular values, Se/Sf (2, n) the exact (e,f) form (None unless requested) and info (n,).
+    ncr: k2svd_?gesvd2_ncr, the variant with a hypot that is not correctly rounded."""
     p = _prefix(G.dtype)
     dev = G.device
     _check(G, "G", G.dtype, dev)
@@ -145,16 +147,24 @@ def gesvd2(G, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_ef=False
             raise K2SVDError("Sf must have the leading dimension of S")
     if info is not None:
         _check(info, "info", torch.int32, dev)
+    name = "k2svd_%sgesvd2%s" % (p, "_ncr" if ncr else "")
     with torch.cuda.device(dev):
-        rc = getattr(lib(), "k2svd_%sgesvd2" % p)(n, _ptr(G), ldg, _ptr(U), ldu, _ptr(V), ldv, _ptr(S), lds,
-                                                  _ptr(Se), _ptr(Sf), _ptr(info), _stream())
+        rc = getattr(lib(), name)(n, _ptr(G), ldg, _ptr(U), ldu, _ptr(V), ldv, _ptr(S), lds,
+                                  _ptr(Se), _ptr(Sf), _ptr(info), _stream())
     if rc != 0:
-        raise K2SVDError("k2svd_%sgesvd2 returned %d" % (p, rc))
+        raise K2SVDError("%s returned %d" % (name, rc))
     return U, V, S, Se, Sf, info
 
 
-def trsvd2(F, Gu, H, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_ef=False, want_info=True):
-    """SVD of the upper-triangular matrices [[F, Gu], [0, H]] given as three (n,) planes."""
+def gesvd2_ncr(G, **kw):
+    """k2svd_?gesvd2_ncr: gesvd2 with the hypot that is not correctly rounded (Alg. 1's branch for it)."""
+    return gesvd2(G, ncr=True, **kw)
+
+
+def trsvd2(F, Gu, H, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_ef=False, want_info=True,
+           ncr=False):
+    """SVD of the upper-triangular matrices [[F, Gu], [0, H]] given as three (n,) planes
+    (ncr: k2svd_?trsvd2_ncr)."""
     p = _prefix(F.dtype)
     dev = F.device
     for t, nm in ((F, "F"), (Gu, "Gu"), (H, "H")):
@@ -173,12 +183,18 @@ def trsvd2(F, Gu, H, U=None, V=None, S=None, Se=None, Sf=None, info=None, want_e
     if want_info and info is None:
         info = torch.empty((n,), dtype=torch.int32, device=dev)
     ldu, ldv, lds = _planes(U, 4, "U"), _planes(V, 4, "V"), _planes(S, 2, "S")
+    name = "k2svd_%strsvd2%s" % (p, "_ncr" if ncr else "")
     with torch.cuda.device(dev):
-        rc = getattr(lib(), "k2svd_%strsvd2" % p)(n, _ptr(F), _ptr(Gu), _ptr(H), _ptr(U), ldu, _ptr(V), ldv,
-                                                  _ptr(S), lds, _ptr(Se), _ptr(Sf), _ptr(info), _stream())
+        rc = getattr(lib(), name)(n, _ptr(F), _ptr(Gu), _ptr(H), _ptr(U), ldu, _ptr(V), ldv,
+                                  _ptr(S), lds, _ptr(Se), _ptr(Sf), _ptr(info), _stream())
     if rc != 0:
-        raise K2SVDError("k2svd_%strsvd2 returned %d" % (p, rc))
+        raise K2SVDError("%s returned %d" % (name, rc))
     return U, V, S, Se, Sf, info
+
+
+def trsvd2_ncr(F, Gu, H, **kw):
+    """k2svd_?trsvd2_ncr: trsvd2 with the hypot that is not correctly rounded."""
+    return trsvd2(F, Gu, H, ncr=True, **kw)
 
 
 def rect_layout(shapes):

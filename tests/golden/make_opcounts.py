@@ -1,6 +1,8 @@
 """Write tests/golden/opcounts.json: the mean algorithmic operation counts per matrix of the
 method (additions, multiplications, fmas, divisions, correctly rounded hypots, eq. (EXT)
-evaluations) on samples of the benchmark workloads, counted by the oracle.
+evaluations, square roots) on samples of the benchmark workloads, counted by the oracle;
+the *_ncr entries count the variant with a hypot that is not correctly rounded (Alg. 1's
+branch for it).
 
 These are the "units of work" of the roofline in bench.py: the method's own operations as
 written in Sect. 3 (exact power-of-two scalings, comparisons and sign changes excluded).
@@ -29,6 +31,10 @@ def main():
             I.general(SAMPLE, SEED + 2, prec, "wide"), prec)
         out["workloads"]["wide_%s_trsvd2" % prec] = oracle.opcount(
             I.triangular(SAMPLE, SEED + 3, prec, "wide"), prec, triangular=True)
+        out["workloads"]["wide_%s_gesvd2_ncr" % prec] = oracle.opcount(
+            I.general(SAMPLE, SEED + 2, prec, "wide"), prec, ncr=True)
+        out["workloads"]["wide_%s_trsvd2_ncr" % prec] = oracle.opcount(
+            I.triangular(SAMPLE, SEED + 3, prec, "wide"), prec, triangular=True, ncr=True)
         out["workloads"]["narrow_%s_gesvd2" % prec] = oracle.opcount(
             I.general(SAMPLE, SEED + 1, prec, "narrow"), prec)
         # complex matrices (Sect. 3.4): real and imaginary planes from two wide-range streams

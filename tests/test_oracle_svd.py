@@ -302,11 +302,11 @@ def test_operation_counts_by_hand():
         if tri:
             return oracle.opcount(np.array(g, dtype=np.float64).reshape(3, 1), triangular=True)
         return oracle.opcount(np.array(g, dtype=np.float64).reshape(4, 1))
-    z = dict(add=0, mul=0, fma=0, div=0, hypot=0, ext=0)
+    z = dict(add=0, mul=0, fma=0, div=0, hypot=0, ext=0, sqrt=0)
     assert count([2.0, 0.0, 0.0, 3.0]) == z
     assert count([2.0, 3.0, 0.0, 0.0]) == dict(z, div=3, hypot=2)
     assert count([2.0, 0.0, 3.0, 0.0]) == dict(z, div=3, hypot=2)
-    tri = dict(add=3, mul=3, fma=1, div=10, hypot=4, ext=0)
+    tri = dict(add=3, mul=3, fma=1, div=10, hypot=4, ext=0, sqrt=0)
     assert count([2.0, 0.0, 1.0, 3.0]) == tri
     assert count([2.0, 1.0, 3.0], tri=True) == tri
-    assert count([2.0, 1.0, 0.5, 3.0]) == dict(add=4, mul=3, fma=4, div=16, hypot=8, ext=1)
+    assert count([2.0, 1.0, 0.5, 3.0]) == dict(add=4, mul=3, fma=4, div=16, hypot=8, ext=1, sqrt=0)
