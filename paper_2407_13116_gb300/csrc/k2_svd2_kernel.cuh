@@ -27,18 +27,30 @@ template <typename T> struct svd_args {
 
 template <typename T> __device__ __forceinline__ T pz(T x) { return unneg0(x); }   // -0 -> +0
 
-// At most 64 registers a thread, so 8 blocks (32 warps) are resident per SM: 5% faster than
-// the unconstrained 80-register build for FP64 on a GB300.
+// Blocks of 256 threads with at most 32 registers a thread, so 8 blocks (64 warps, the full
+// occupancy) are resident per SM.  The rest of the FP64 state spills to local memory (L1):
+// on a GB300 this is 7% faster than 64 registers at half occupancy (which was 5% faster than
+// the unconstrained 80-register build), as the extra warps hide the instruction-fetch
+// stalls of the divergent method.  One exception, also measured: the triangular FP64 kernel
+// of the variant with the hypot that is not correctly rounded runs 2.8 times slower at 32
+// registers than at 64, so it keeps blocks of 128 threads (8 per SM, 64 registers).
+template <typename T, bool TRI, bool NCR> constexpr int svd2_threads()
+{
+    return (sizeof(T) == 8 && TRI && NCR) ? 128 : 256;
+}
 // NCR: the method with the hypot that is not correctly rounded (Alg. 1's branch for it).
+// Inputs and outputs are touched once: streaming loads and stores (__ldcs, __stcs) keep them
+// from evicting the spilled registers from L2, which cut the kernel's DRAM traffic by a
+// quarter (reads down to the input bytes) at the same speed.
 template <typename T, bool TRI, bool NCR>
-__global__ void __launch_bounds__(128, 8) svd2_kernel(const svd_args<T> a)
+__global__ void __launch_bounds__(svd2_threads<T, TRI, NCR>(), 8) svd2_kernel(const svd_args<T> a)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const T g11 = a.g0[i];
-        const T g21 = TRI ? T(0) : a.g1[i];
-        const T g12 = a.g2[i];
-        const T g22 = a.g3[i];
+        const T g11 = __ldcs(a.g0 + i);
+        const T g21 = TRI ? T(0) : __ldcs(a.g1 + i);
+        const T g12 = __ldcs(a.g2 + i);
+        const T g22 = __ldcs(a.g3 + i);
         svd2_out<T> o;
         if (is_fin(g11) && is_fin(g21) && is_fin(g12) && is_fin(g22)) {
             svd2<T, !TRI, NCR>(g11, g21, g12, g22, o);         // general matrices leave the FP64 pipe room
@@ -49,16 +61,16 @@ __global__ void __launch_bounds__(128, 8) svd2_kernel(const svd_args<T> a)
             o.s1.e = o.s2.e = 0; o.s1.f = o.s2.f = qn;
             o.info = -1;
         }
-        a.u0[i] = pz(o.U.a11); a.u1[i] = pz(o.U.a21); a.u2[i] = pz(o.U.a12); a.u3[i] = pz(o.U.a22);
-        a.v0[i] = pz(o.V.a11); a.v1[i] = pz(o.V.a21); a.v2[i] = pz(o.V.a12); a.v3[i] = pz(o.V.a22);
+        __stcs(a.u0 + i, pz(o.U.a11)); __stcs(a.u1 + i, pz(o.U.a21)); __stcs(a.u2 + i, pz(o.U.a12)); __stcs(a.u3 + i, pz(o.U.a22));
+        __stcs(a.v0 + i, pz(o.V.a11)); __stcs(a.v1 + i, pz(o.V.a21)); __stcs(a.v2 + i, pz(o.V.a12)); __stcs(a.v3 + i, pz(o.V.a22));
         if (o.info >= 0) {
-            a.s1[i] = ef_fl(o.s1); a.s2[i] = ef_fl(o.s2);
+            __stcs(a.s1 + i, ef_fl(o.s1)); __stcs(a.s2 + i, ef_fl(o.s2));
         } else {
-            a.s1[i] = o.s1.f; a.s2[i] = o.s2.f;
+            __stcs(a.s1 + i, o.s1.f); __stcs(a.s2 + i, o.s2.f);
         }
-        if (a.se1) { a.se1[i] = o.s1.e; a.se2[i] = o.s2.e; }
-        if (a.sf1) { a.sf1[i] = o.s1.f; a.sf2[i] = o.s2.f; }
-        if (a.info) a.info[i] = o.info;
+        if (a.se1) { __stcs(a.se1 + i, o.s1.e); __stcs(a.se2 + i, o.s2.e); }
+        if (a.sf1) { __stcs(a.sf1 + i, o.s1.f); __stcs(a.sf2 + i, o.s2.f); }
+        if (a.info) __stcs(a.info + i, o.info);
     }
 }
 
@@ -70,12 +82,13 @@ static int launch(const svd_args<T> &a, cudaStream_t st)
     if (cudaGetDevice(&dev) != cudaSuccess) return K2SVD_ECUDA;
     if (dev != cached_dev) {
         int nb = 0;
-        if (grid_for(svd2_kernel<T, TRI, NCR>, 128, 0, &nb) != 0) return K2SVD_ECUDA;
+        if (grid_for(svd2_kernel<T, TRI, NCR>, svd2_threads<T, TRI, NCR>(), 0, &nb) != 0) return K2SVD_ECUDA;
         cached_dev = dev; cached_blocks = nb;
     }
-    int64_t need = (a.n + 127) / 128;
+    constexpr int nt = svd2_threads<T, TRI, NCR>();
+    int64_t need = (a.n + nt - 1) / nt;
     int blocks = (int)(need < cached_blocks ? need : cached_blocks);
-    svd2_kernel<T, TRI, NCR><<<blocks, 128, 0, st>>>(a);
+    svd2_kernel<T, TRI, NCR><<<blocks, nt, 0, st>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : K2SVD_ECUDA;
 }
 
