@@ -164,8 +164,8 @@ class Clocks:
 # dram__bytes_write.sum) of `python bench.py --profile-case d` (2^22 matrices), scaled by
 # the matrix count to a full 2^27-matrix launch.  Valid only for the kernel sources with
 # this hash; any change to them reports null until a new capture is taken.
-TRAFFIC_SRC_HASH = "285a7748757ff807"
-TRAFFIC_BYTES_PER_MATRIX = (137.791232e6 + 620.964864e6) / (1 << 22)
+TRAFFIC_SRC_HASH = "6187dd399f2925fc"
+TRAFFIC_BYTES_PER_MATRIX = (136.719616e6 + 291.307776e6 + 201.474304e6 + 344.086272e6) / (1 << 22)
 KERNEL_SOURCES = ("k2_fp.cuh", "k2_svd2.cuh", "k2_svd2_kernel.cuh", "k2_gesvd2.cu")
 
 
@@ -721,7 +721,7 @@ def run_ours(a):
     traffic = TRAFFIC_BYTES_PER_MATRIX * N_HALF_D if kernel_hash() == TRAFFIC_SRC_HASH else None
     roofline = {"bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9,
                 "unit": "G FP64-pipe op/s", "frac": ach / peak, "traffic": traffic,
-                "kernel": "svd2_kernel<double,false> (k2svd_dgesvd2)",
+                "kernel": "svd2a_kernel + svd2b_kernel<double> (k2svd_dgesvd2: phases 1-2, then phase 3)",
                 "kernel_ms": res["ge_ms"], "ops_per_matrix": cost_ge,
                 "algorithmic_bytes": BYTES_GE["d"] * N_HALF_D,
                 "peak_source": "nominal: SMs x 2 DFMA/clk x median SM clock %.0f MHz during the timed region; "

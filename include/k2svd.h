@@ -10,6 +10,8 @@
  * Pointers.  Every array argument is a DEVICE pointer (cudaMalloc'd or managed
  *   memory), owned by the caller; the library never allocates, frees or keeps them.
  *   Optional arrays are marked "nullable" and are skipped when NULL.
+ * Library memory.  Only k2svd_dgesvd2 on 65536 or more matrices allocates: stream-ordered
+ *   scratch from a private pool (see there); k2svd_dkogbet_noalloc uses a static array.
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *   stream).  Calls are asynchronous and stream-ordered; a return value of 0 means
  *   the work was enqueued.  Kernel faults surface as CUDA errors on that stream.
@@ -73,6 +75,11 @@ extern "C" {
  *   stream  cudaStream_t as void*
  * Planes of different arrays must not overlap.  Argument order for error codes:
  * 1 batch, 2 G, 3 ldg, 4 U, 5 ldu, 6 V, 7 ldv, 8 S, 9 lds.
+ * k2svd_dgesvd2 on 65536 or more matrices runs the method as two kernels (phases 1-2, then
+ * phase 3) with their intermediate state in a scratch buffer of 48 bytes per matrix (at most
+ * 2^24 matrices at a time, 805 MB), allocated in stream order on `stream` from a private
+ * memory pool of the library that keeps up to 1 GiB between calls; if no scratch can be had
+ * it runs the single fused kernel.  The results are the same bits either way.
  */
 int k2svd_dgesvd2(int64_t batch, const double *G, int64_t ldg,
                   double *U, int64_t ldu, double *V, int64_t ldv,

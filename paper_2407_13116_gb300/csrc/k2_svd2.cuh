@@ -271,6 +271,169 @@ __device__ __forceinline__ void phase1(T &g11, T &g21, T &g12, T &g22, int extra
     tp = !eq0(g11) | (!eq0(g21) << 1) | (!eq0(g12) << 2) | (!eq0(g22) << 3);
 }
 
+// What phase 3 (Sect. 3.3) needs from phases 1 and 2: R and the transformations already
+// applied.  Class 13: R = [[r11, r12], [0, r22]] after the permutations P_U, P_V and the
+// signs S11 (na), S12, S22 of Sect. 3.2.1.  Class 15: R' after S12 and S22, with tan and
+// sec of theta (eq. (QR15)), P_U, P_V and the row signs S1 (na, nb) of Sect. 3.2.2.
+template <typename T> struct svd2_mid {
+    T r11, r12, r22, tth, secth;
+    int s, t, tp, flags;
+    bool c15, pu, pv, na, nb, n12, n22;
+};
+
+// Phases 1 and 2 (Sect. 3.1, 3.2).  Returns false when o is complete (the simple classes,
+// the fallback of Sect. 3.2.2), true when phase 3 (svd2_b) must finish from m.  FDIV: the
+// quotients of eq. (QR15) (tan theta, r12, r22) on the FP64 divider (see csdiv).
+template <typename T, bool NCR = false, bool FDIV = false>
+__device__ __forceinline__ bool svd2_a(T g11, T g21, T g12, T g22, svd2_out<T> &o, svd2_mid<T> &m)
+{
+    int t, s, tp, flags = 0;
+    phase1(g11, g21, g12, g22, 0, t, s, tp);
+    const int clsp = cls_of(tp);
+    m.s = s; m.t = t; m.tp = tp;
+    T d1 = T(0), d2 = T(0);
+
+    if (clsp == 9) {
+        simple9(tp, g11, g21, g12, g22, o.U, o.V, d1, d2);
+    } else if (clsp == 3 || clsp == 5) {
+        simple35<T, NCR>(tp, g11, g21, g12, g22, o.U, o.V, d1);
+    } else if (clsp == 13) {
+        // Sect. 3.2.1: permute to upper triangular, signs of row 1, column 2, row 2
+        m.pu = (tp == 11 || tp == 14); m.pv = (tp == 7 || tp == 11);
+        T a, b, d;
+        if (tp == 7) { a = g12; b = g11; d = g21; }
+        else if (tp == 11) { a = g22; b = g21; d = g11; }
+        else if (tp == 14) { a = g21; b = g22; d = g12; }
+        else { a = g11; b = g12; d = g22; }
+        m.na = lt0(a); a = absv(a); if (m.na) b = ngt(b);
+        m.n12 = lt0(b); b = absv(b); if (m.n12) d = ngt(d);
+        m.n22 = lt0(d); d = absv(d);
+        m.r11 = a; m.r12 = b; m.r22 = d;
+        m.c15 = false; m.nb = false; m.flags = flags;
+        return true;
+    } else {
+        // Sect. 3.2.2: fully pivoted URV of a matrix without zeros
+        T w1 = hyp<NCR>(g11, g21), w2 = hyp<NCR>(g12, g22);
+        const bool pv = pos_lt(w1, w2);
+        if (pv) { T x = g11; g11 = g12; g12 = x; x = g21; g21 = g22; g22 = x; w1 = w2; }
+        const bool n1a = lt0(g11), n1b = lt0(g21);            // S1
+        if (n1a) { g11 = ngt(g11); g12 = ngt(g12); }
+        if (n1b) { g21 = ngt(g21); g22 = ngt(g22); }
+        const bool pu = pos_lt(g11, g21);
+        if (pu) { T x = g11; g11 = g21; g21 = x; x = g12; g12 = g22; g22 = x; }
+        // eq. (QR15)
+        const T tth = csdiv<FDIV>(g21, g11);
+        const T secth = hyp<NCR>(tth, T(1));
+        T r11 = w1, r12, r22;
+        if (eq0(fma(tth, g11, ngt(g21)))) {                // tan(theta) exact: Lemma 3.4
+            r12 = csdiv<FDIV>(fma(g22, tth, g12), secth);
+            r22 = csdiv<FDIV>(fma(ngt(g12), tth, g22), secth);
+        } else if (lt0(g12) == lt0(g22)) {         // Thm. 3.5: r22 by eq. (EXT)
+            r12 = csdiv<FDIV>(fma(g22, tth, g12), secth);
+            r22 = csdiv<FDIV>(ext_num_div(g22, g11, g12, g21, true, g11), secth);
+            flags |= FL_EXT;
+        } else {                                           // Thm. 3.5: r12 by eq. (EXT)
+            r22 = csdiv<FDIV>(fma(ngt(g12), tth, g22), secth);
+            r12 = csdiv<FDIV>(ext_num_div(g12, g11, g22, g21, false, g11), secth);
+            flags |= FL_EXT;
+        }
+        if (eq0(r12) || eq0(r22)) {
+            // R'' of type 9 (or 1) or 5: finish as Sect. 3.1, G' = S1 P_U U_theta R'' P_V^T
+            flags |= FL_FALLBACK;
+            const T cth = qdiv(T(1), secth), sth = qdiv(tth, secth);
+            m22<T> Ur, Vr;
+            if (eq0(r12)) {
+                simple9<T>(!eq0(r22) ? 9 : 1, r11, T(0), T(0), r22, Ur, Vr, d1, d2);
+            } else {
+                simple35<T, NCR>(5, r11, T(0), r12, T(0), Ur, Vr, d1);
+                d2 = T(0);
+            }
+            // U_theta Ur, with Ur a signed permutation: pick and negate columns of U_theta
+            m22<T> M;
+            bool c0first = !eq0(Ur.a11);                 // non-zero of column 0 in row 0
+            T sg0 = c0first ? Ur.a11 : Ur.a21, sg1 = c0first ? Ur.a22 : Ur.a12;
+            T u0a = c0first ? cth : ngt(sth), u0b = c0first ? sth : cth;   // U_theta column k0
+            T u1a = c0first ? ngt(sth) : cth, u1b = c0first ? cth : sth;   // U_theta column k1
+            M.a11 = lt0(sg0) ? ngt(u0a) : u0a; M.a21 = lt0(sg0) ? ngt(u0b) : u0b;
+            M.a12 = lt0(sg1) ? ngt(u1a) : u1a; M.a22 = lt0(sg1) ? ngt(u1b) : u1b;
+            if (pu) swap_rows(M);
+            if (n1a) neg_row(M, 0);
+            if (n1b) neg_row(M, 1);
+            o.U = M;
+            if (pv) swap_rows(Vr);
+            o.V = Vr;
+        } else {
+            m.n12 = lt0(r12);
+            if (m.n12) { r12 = ngt(r12); r22 = ngt(r22); }        // R'' S12
+            m.n22 = lt0(r22);
+            if (m.n22) r22 = ngt(r22);                         // S22 R'
+            m.r11 = r11; m.r12 = r12; m.r22 = r22; m.tth = tth; m.secth = secth;
+            m.c15 = true; m.pu = pu; m.pv = pv; m.na = n1a; m.nb = n1b; m.flags = flags;
+            return true;
+        }
+    }
+    o.s1 = ef_pow2(-s, ef_of(d1));                         // Sect. 3.3.2: 2^-s (.) sigma~'
+    o.s2 = ef_pow2(-s, ef_of(d2));
+    o.info = t | (tp << 4) | (flags << 8);
+    return false;
+}
+
+// Phase 3 (Sect. 3.3) from the state of svd2_a: the SVD of R by Alg. 1 and Alg. 2, the
+// assembly of U and V (class 15 with the heuristic of eqs. (p+t), (p-t), (tan+-), (UV)),
+// and the backscaling.  FDIV: see csdiv.
+template <typename T, bool FDIV = false, bool NCR = false>
+__device__ __forceinline__ void svd2_b(const svd2_mid<T> &m, svd2_out<T> &o)
+{
+    int flags = m.flags;
+    tri_out<T> z;
+    tri_svd<T, FDIV, NCR>(m.r11, m.r12, m.r22, z, flags);
+    m22<T> V = vcheck(z);                                  // V = P_V S12 V-check
+    if (m.n12) neg_row(V, 1);
+    if (m.pv) swap_rows(V);
+    o.V = V;
+    if (!m.c15) {
+        m22<T> U = ucheck(z);                              // U = P_U S11 S22 U-check
+        if (m.na) neg_row(U, 0);
+        if (m.n22) neg_row(U, 1);
+        if (m.pu) swap_rows(U);
+        o.U = U;
+    } else {
+        // U = S1 P_U S22 U(phi +- theta) S2 P_sigma: eqs. (p+t), (p-t), (tan+-), (UV)
+        const T tth = m.tth, secth = m.secth;
+        const bool plus = !m.n22;
+        const T tb = z.swap ? qdiv(T(1), z.tanpsi) : z.tanphi;
+        T ca, sa;
+        if (is_inf(tb)) {
+            const T cth = qdiv(T(1), secth), sth = qdiv(tth, secth);
+            ca = plus ? ngt(sth) : sth; sa = cth;
+        } else {
+            const T N = plus ? tb + tth : tb - tth;
+            const T D = plus ? fma(ngt(tb), tth, T(1)) : fma(tb, tth, T(1));
+            if (eq0(D)) { ca = T(0); sa = lt0(N) ? T(-1) : T(1); }
+            else {
+                const T ta = qdiv(N, D);
+                if (is_inf(ta)) { ca = T(0); sa = lt0(N) ? T(-1) : T(1); }
+                else {
+                    T c0, s0;
+                    cos_sin<NCR>(ta, c0, s0);
+                    if (lt0(D)) { ca = ngt(c0); sa = ngt(s0); } else { ca = c0; sa = s0; }
+                }
+            }
+        }
+        m22<T> U = rot(ca, sa);
+        if (z.swap) neg_col(U, 1);                         // S2
+        if (m.n22) neg_row(U, 1);                          // S22
+        if (m.pu) swap_rows(U);                            // P_U
+        if (m.na) neg_row(U, 0);                           // S1
+        if (m.nb) neg_row(U, 1);
+        if (z.psig) swap_cols(U);                          // P_sigma
+        o.U = U;
+    }
+    o.s1 = ef_pow2(-m.s, z.s1);                            // Sect. 3.3.2: 2^-s (.) sigma~'
+    o.s2 = ef_pow2(-m.s, z.s2);
+    o.info = m.t | (m.tp << 4) | (flags << 8);
+}
+
 // FDIV: see csdiv; the results do not depend on it.  NCR: see tri_svd.
 template <typename T, bool FDIV = false, bool NCR = false>
 __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
