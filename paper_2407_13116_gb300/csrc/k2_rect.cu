@@ -49,6 +49,10 @@ template <typename T> struct rect_params {
     int32_t *kscale;                    // per matrix
 };
 
+// B and the Q being formed are row-major in the workspace (element (r, c) at r q + c): each
+// thread owns columns and walks down them in row order, as the fixed operation order asks,
+// and at every row the threads of a warp touch consecutive addresses.  Q is then copied
+// column-major into B's place for the assembly.
 template <typename T>
 __global__ void __launch_bounds__(128) qrcp_kernel(const rect_params<T> P)
 {
@@ -64,7 +68,7 @@ __global__ void __launch_bounds__(128) qrcp_kernel(const rect_params<T> P)
         __syncthreads();
         int le = INT_MIN;
         for (int64_t e = tid; e < (int64_t)p * q; e += nt) {
-            const int c = (int)(e / p), r = (int)(e % p);
+            const int r = (int)(e / q), c = (int)(e % q);
             const T x = d.tr ? A[(int64_t)r * d.m + c] : A[(int64_t)c * d.m + r];
             B[e] = x;
             if (is_fin(x) && !eq0(x)) le = max(le, fpt<T>::expo(x));
@@ -78,9 +82,8 @@ __global__ void __launch_bounds__(128) qrcp_kernel(const rect_params<T> P)
         __syncthreads();
         for (int j = 0; j < q; ++j) {
             for (int c = j + tid; c < q; c += nt) {
-                const T *col = B + (int64_t)c * p;
                 T sq = T(0);
-                for (int r = j; r < p; ++r) sq = fma(col[r], col[r], sq);
+                for (int r = j; r < p; ++r) { const T b = B[(int64_t)r * q + c]; sq = fma(b, b, sq); }
                 nrm[c] = sq;
             }
             __syncthreads();
@@ -92,12 +95,14 @@ __global__ void __launch_bounds__(128) qrcp_kernel(const rect_params<T> P)
             __syncthreads();
             const int piv = s_piv;
             if (piv != j) {
-                T *cj = B + (int64_t)j * p, *cp = B + (int64_t)piv * p;
-                for (int r = tid; r < p; r += nt) { const T t = cj[r]; cj[r] = cp[r]; cp[r] = t; }
+                for (int r = tid; r < p; r += nt) {
+                    T *row = B + (int64_t)r * q;
+                    const T t = row[j]; row[j] = row[piv]; row[piv] = t;
+                }
                 if (tid == 0) { const int t = perm[j]; perm[j] = perm[piv]; perm[piv] = t; }
             }
             __syncthreads();
-            T *x = B + (int64_t)j * p + j;
+            T *x = B + (int64_t)j * q + j;                     // x[i q] = element (j + i, j)
             const int L = p - j;
             if (tid == 0) {
                 if (nrm[piv] == T(0)) { vv[j] = T(0); alph[j] = x[0]; }
@@ -114,39 +119,44 @@ __global__ void __launch_bounds__(128) qrcp_kernel(const rect_params<T> P)
             const T w = vv[j];
             if (w != T(0)) {
                 for (int c = j + 1 + tid; c < q; c += nt) {
-                    T *y = B + (int64_t)c * p + j;
+                    T *y = B + (int64_t)j * q + c;                 // y[i q] = element (j + i, c)
                     T s = x[0] * y[0];
-                    for (int i = 1; i < L; ++i) s = fma(x[i], y[i], s);
+                    for (int i = 1; i < L; ++i) s = fma(x[(int64_t)i * q], y[(int64_t)i * q], s);
                     const T f = (s + s) / w;
-                    for (int i = 0; i < L; ++i) y[i] = fma(-f, x[i], y[i]);
+                    for (int i = 0; i < L; ++i) y[(int64_t)i * q] = fma(-f, x[(int64_t)i * q], y[(int64_t)i * q]);
                 }
             }
             __syncthreads();
         }
-        // R (q x q, packed for the n x n driver) and Q = H_0 ... H_{q-1} [I; 0]
+        // R (q x q column-major, packed for the n x n driver) and Q = H_0 ... H_{q-1} [I; 0]
         T *R = P.R + d.roff;
         for (int64_t e = tid; e < (int64_t)q * q; e += nt) {
             const int c = (int)(e / q), r = (int)(e % q);
-            R[e] = r < c ? B[(int64_t)c * p + r] : (r == c ? alph[c] : T(0));
+            R[e] = r < c ? B[(int64_t)r * q + c] : (r == c ? alph[c] : T(0));
         }
         for (int64_t e = tid; e < (int64_t)p * q; e += nt) {
-            const int c = (int)(e / p), r = (int)(e % p);
+            const int r = (int)(e / q), c = (int)(e % q);
             Q[e] = r == c ? T(1) : T(0);
         }
         __syncthreads();
         for (int j = q - 1; j >= 0; --j) {
             const T w = vv[j];
             if (w == T(0)) continue;
-            const T *x = B + (int64_t)j * p + j;
+            const T *x = B + (int64_t)j * q + j;
             const int L = p - j;
             for (int c = tid; c < q; c += nt) {
-                T *y = Q + (int64_t)c * p + j;
+                T *y = Q + (int64_t)j * q + c;
                 T s = x[0] * y[0];
-                for (int i = 1; i < L; ++i) s = fma(x[i], y[i], s);
+                for (int i = 1; i < L; ++i) s = fma(x[(int64_t)i * q], y[(int64_t)i * q], s);
                 const T f = (s + s) / w;
-                for (int i = 0; i < L; ++i) y[i] = fma(-f, x[i], y[i]);
+                for (int i = 0; i < L; ++i) y[(int64_t)i * q] = fma(-f, x[(int64_t)i * q], y[(int64_t)i * q]);
             }
             __syncthreads();
+        }
+        // Q column-major into B's place (the reflectors are no longer needed)
+        for (int64_t e = tid; e < (int64_t)p * q; e += nt) {
+            const int c = (int)(e / p), r = (int)(e % p);
+            B[e] = Q[(int64_t)r * q + c];
         }
         __syncthreads();
     }
@@ -159,7 +169,8 @@ __global__ void __launch_bounds__(256) rect_assemble_kernel(const rect_params<T>
     for (int mi = blockIdx.x; mi < P.count; mi += gridDim.x) {
         const rect_desc d = P.desc[mi];
         const int p = d.p, q = d.q, tid = threadIdx.x, nt = blockDim.x;
-        const T *Q = P.Q + d.boff, *UR = P.UR + d.roff, *VR = P.VR + d.roff, *SR = P.SR + d.sroff;
+        const T *Q = P.B + d.boff;                        // column-major Q, left there by qrcp_kernel
+        const T *UR = P.UR + d.roff, *VR = P.VR + d.roff, *SR = P.SR + d.sroff;
         const int32_t *perm = P.perm + d.woff;
         T *QU = d.tr ? P.V + d.voff : P.U + d.uoff;
         T *PV = d.tr ? P.U + d.uoff : P.V + d.voff;
