@@ -421,6 +421,20 @@ def kog_leg(steps, warmup, dev, D):
     torch.cuda.synchronize()
     plain_ms = D.max((time.perf_counter() - t) * 1e3)
     same = bool(torch.equal(Sp, S))
+    # the dynamic pivot ordering (persistent graph form), same matrices and stopping rule
+    wsd = k2svd.kogbet_workspace(orders, torch.float64, k2svd.KOG_GRAPH | k2svd.KOG_DYNAMIC, dev)
+    for _ in range(warmup + 1):
+        run(k2svd.KOG_GRAPH | k2svd.KOG_DYNAMIC, wsd)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        run(k2svd.KOG_GRAPH | k2svd.KOG_DYNAMIC, wsd)
+    e1.record()
+    torch.cuda.synchronize()
+    dyn_ms = D.max(e0.elapsed_time(e1) / steps)
+    dyn_sweeps = sw.cpu().numpy().astype(np.int64)
+    dyn_conv = int((info.cpu().numpy() == 0).sum())
+    del wsd
     nn = orders.astype(np.int64)
     # method's FP64 work: per sweep n(n-1)/2 pivots, each a 2x2 SVD (~239 FP64 slots, the
     # general double count) and 16 FP64 operations per index (row, column, U and V rotations)
@@ -434,8 +448,11 @@ def kog_leg(steps, warmup, dev, D):
             "roofline": {"bound": "alu", "achieved": ops / (pers_ms / 1e3) / 1e9, "peak": peak / 1e9,
                          "unit": "G FP64-pipe op/s", "frac": ops / (pers_ms / 1e3) / peak,
                          "ops": ops},
+            "dynamic_ordering": {"persistent_ms": dyn_ms, "speedup_vs_per_step": plain_ms / dyn_ms,
+                                 "vs_modulus_persistent": pers_ms / dyn_ms, "mean_sweeps": float(dyn_sweeps.mean()),
+                                 "max_sweeps": int(dyn_sweeps.max()), "converged": dyn_conv},
             "workload": "8192 FP64 Q1 diag(sigma) Q2^T, n uniform in {8..128}, sigma log-uniform [1e-12,1], "
-                        "modulus strategy, off < n eps ||G||_F"}
+                        "modulus strategy (and the dynamic ordering beside it), off < n eps ||G||_F"}
 
 
 def phases_leg(steps, warmup, dev, D, rates, clk_mhz, oc):

@@ -311,7 +311,14 @@ int k2svd_sgesvd2_bwd(int64_t batch, const float *U, const float *S, const float
  *   flags        K2SVD_KOG_PLAIN: one launch per step (the per-step form, for comparison);
  *                K2SVD_KOG_GRAPH: capture the launches in a CUDA graph (cached for repeated
  *                calls with the same arguments) and launch the graph;
- *                K2SVD_KOG_NOTUNE: skip the block-size autotuner (defaults per order)
+ *                K2SVD_KOG_NOTUNE: skip the block-size autotuner (defaults per order);
+ *                K2SVD_KOG_DYNAMIC: the dynamic ordering instead of the modulus strategy
+ *                (Sect. 1 names it as a candidate): the pairs of a step are taken greedily
+ *                by decreasing weight w_ij = fma(g_ji, g_ji, g_ij^2) computed from G_k (ties:
+ *                smaller i, then smaller j), each pair whose indices are both still free,
+ *                up to floor(n/2) pairs; a sweep is still n steps.  Persistent form only
+ *                (with K2SVD_KOG_PLAIN: error -13); the workspace grows by n(n-1)/2
+ *                elements per matrix
  *   workspace    device scratch of ws_bytes bytes, 256-byte aligned, from k2svd_?kogbet_ws
  *                for the same batch, n and flags; owned by the caller, not kept after the call
  *                (a cached graph refers to it: keep it alive while reusing the same arguments)
@@ -325,6 +332,7 @@ int k2svd_sgesvd2_bwd(int64_t batch, const float *U, const float *S, const float
 #define K2SVD_KOG_PLAIN  1
 #define K2SVD_KOG_GRAPH  2
 #define K2SVD_KOG_NOTUNE 4
+#define K2SVD_KOG_DYNAMIC 8
 int k2svd_dkogbet_ws(int64_t batch, const int32_t *n, int32_t flags, size_t *ws_bytes);
 int k2svd_skogbet_ws(int64_t batch, const int32_t *n, int32_t flags, size_t *ws_bytes);
 int k2svd_dkogbet(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs,

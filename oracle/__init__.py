@@ -9,7 +9,7 @@ Functions whose result is not pinned by an independent check are marked
 "parity unpinned" in their docstrings.
 """
 from .k2ref import (build, lib, gesvd2, trsvd2, cgesvd2, hypot, hypot_n, hypot_ncr, hypot_ncr_n, prescale2, lasv2, trace, efops, prec, effl, ext,
-                    brute_sigma, dmetrics, FLAGS, opcount, OPS, gesvd2_bwd, kogbet, kog_sigma_bwd, gesvdr)
+                    brute_sigma, dmetrics, FLAGS, opcount, OPS, gesvd2_bwd, kogbet, kog_sigma_bwd, gesvdr, dyn_pairs)
 
 __all__ = ["build", "lib", "gesvd2", "trsvd2", "cgesvd2", "hypot", "hypot_n", "hypot_ncr", "hypot_ncr_n", "prescale2", "lasv2", "trace", "efops", "prec", "effl",
-           "ext", "brute_sigma", "dmetrics", "FLAGS", "opcount", "OPS", "gesvd2_bwd", "kogbet", "kog_sigma_bwd", "gesvdr"]
+           "ext", "brute_sigma", "dmetrics", "FLAGS", "opcount", "OPS", "gesvd2_bwd", "kogbet", "kog_sigma_bwd", "gesvdr", "dyn_pairs"]

@@ -101,8 +101,12 @@ def _bind_extra(L):
     """Bindings of the n x n driver and the backward reference, when compiled in."""
     P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
     for sfx in ("d", "s"):
-        fn = getattr(L, "k2ref_kogbet_" + sfx)
-        fn.argtypes = [I32, P, P, P, P, C.c_int, D, P, P]
+        for nm in ("k2ref_kogbet_", "k2ref_kogbet_dyn_"):
+            fn = getattr(L, nm + sfx)
+            fn.argtypes = [I32, P, P, P, P, C.c_int, D, P, P]
+            fn.restype = C.c_int
+        fn = getattr(L, "k2ref_dyn_pairs_" + sfx)
+        fn.argtypes = [I32, P, P, P]
         fn.restype = C.c_int
         getattr(L, "k2ref_kog_sigma_bwd_" + sfx).argtypes = [I32, P, P, P, P]
     if hasattr(L, "k2ref_gesvd2_bwd_d"):
@@ -290,19 +294,31 @@ def gesvd2_bwd(U, S, V, dS=None, dU=None, dV=None, tau=1e-10):
     return dG
 
 
-def kogbet(A, prec="d", max_sweeps=40, tol_factor=1.0):
+def kogbet(A, prec="d", max_sweeps=40, tol_factor=1.0, dynamic=False):
     """n x n Kogbetliantz SVD of one square matrix (column-major / any numpy array):
-    returns (U, S, V, sweeps, info) with A ~ U diag(S) V^T, S descending."""
+    returns (U, S, V, sweeps, info) with A ~ U diag(S) V^T, S descending.  dynamic: the
+    dynamic pivot ordering instead of the modulus strategy."""
     T = _dt(prec)
     A = np.asfortranarray(A, dtype=T)
     n = A.shape[0]
     U = np.empty((n, n), T, order="F"); V = np.empty((n, n), T, order="F"); S = np.empty(n, T)
     sw = C.c_int32(0); info = C.c_int32(0)
-    rc = getattr(lib(), "k2ref_kogbet_" + prec)(n, _ptr(A), _ptr(U), _ptr(V), _ptr(S), int(max_sweeps),
-                                                 float(tol_factor), C.byref(sw), C.byref(info))
+    fn = getattr(lib(), ("k2ref_kogbet_dyn_" if dynamic else "k2ref_kogbet_") + prec)
+    rc = fn(n, _ptr(A), _ptr(U), _ptr(V), _ptr(S), int(max_sweeps), float(tol_factor), C.byref(sw), C.byref(info))
     if rc != 0:
         raise ValueError("k2ref_kogbet returned %d" % rc)
     return U, S, V, sw.value, info.value
+
+
+def dyn_pairs(G, prec="d"):
+    """The pivot pairs of one step of the dynamic ordering taken on the square matrix G, in
+    the order taken: a list of (i, j)."""
+    T = _dt(prec)
+    G = np.asfortranarray(G, dtype=T)
+    n = G.shape[0]
+    pi = np.zeros(max(n, 1), np.int32); pj = np.zeros(max(n, 1), np.int32)
+    np_ = getattr(lib(), "k2ref_dyn_pairs_" + prec)(n, _ptr(G), _ptr(pi), _ptr(pj))
+    return [(int(pi[p]), int(pj[p])) for p in range(np_)]
 
 
 def gesvdr(A, prec="d", max_sweeps=40, tol_factor=1.0):

@@ -21,6 +21,12 @@
  *    sweep has touched it) is negated together with column i of U (signs go to the left,
  *    as in Sect. 3.1), then the diagonal is sorted into descending order (stable),
  *    permuting U and V.
+ * The dynamic ordering (Sect. 1 names it as a candidate parallel strategy) replaces the
+ * modulus pairs of a step: every pair i < j gets the weight w_ij = fma(g_ji, g_ji, g_ij^2)
+ * from G_k, the pairs are ranked by decreasing weight (ties: smaller i, then smaller j),
+ * and the ranked list is scanned once, each pair whose two indices are both still free
+ * being taken, until floor(n/2) pairs are taken.  A "sweep" is still n such steps, with
+ * the same convergence test before each.
  */
 #include <math.h>
 #include <stdint.h>
@@ -31,6 +37,36 @@ void k2ref_pivot_d(double g11, double g21, double g12, double g22, double u[4], 
 void k2ref_pivot_s(float g11, float g21, float g12, float g22, float u[4], float v[4], float s[2]);
 
 #define KOG_BODY(R, SFX, PIVOT, FMA, SQRT, SCALBN, ILOGB, EPS)                                      \
+typedef struct { R w; int i, j; } SFX(wpair);                                                     \
+static int SFX(wcmp)(const void *pa, const void *pb)          /* decreasing w, then (i, j) */     \
+{                                                                                                 \
+    const SFX(wpair) *a = (const SFX(wpair) *)pa, *b = (const SFX(wpair) *)pb;                    \
+    if (a->w != b->w) return a->w > b->w ? -1 : 1;                                                \
+    if (a->i != b->i) return a->i < b->i ? -1 : 1;                                                \
+    return a->j < b->j ? -1 : (a->j > b->j);                                                      \
+}                                                                                                 \
+/* The pairs of one step of the dynamic ordering from G (column-major, order n): np pairs */    \
+/* (pi[p], pj[p]) in the order taken. */                                                        \
+int SFX(k2ref_dyn_pairs)(int32_t n, const R *G, int32_t *pi, int32_t *pj)                         \
+{                                                                                                 \
+    size_t m = (size_t)n * (size_t)(n - 1) / 2, q = 0;                                            \
+    SFX(wpair) *L = (SFX(wpair) *)malloc(sizeof(SFX(wpair)) * (m ? m : 1));                       \
+    char *used = (char *)calloc((size_t)n, 1);                                                    \
+    for (int i = 0; i < n; ++i)                                                                   \
+        for (int j = i + 1; j < n; ++j) {                                                         \
+            R gij = G[(size_t)j * n + i], gji = G[(size_t)i * n + j];                             \
+            L[q].w = FMA(gji, gji, gij * gij); L[q].i = i; L[q].j = j; ++q;                       \
+        }                                                                                         \
+    qsort(L, m, sizeof(SFX(wpair)), SFX(wcmp));                                                   \
+    int np = 0;                                                                                   \
+    for (size_t e = 0; e < m && np < n / 2; ++e)                                                  \
+        if (!used[L[e].i] && !used[L[e].j]) {                                                     \
+            used[L[e].i] = used[L[e].j] = 1;                                                      \
+            pi[np] = L[e].i; pj[np] = L[e].j; ++np;                                               \
+        }                                                                                         \
+    free(L); free(used);                                                                          \
+    return np;                                                                                    \
+}                                                                                                 \
 static R SFX(colsq)(const R *G, int n, int skip_diag)                                             \
 {                                                                                                 \
     R tot = 0;                                                                                    \
@@ -48,8 +84,8 @@ static void SFX(rot)(R *x, R *y, const R m[4])                                  
     *x = FMA(m[1], b, m[0] * a);                                                                  \
     *y = FMA(m[3], b, m[2] * a);                                                                  \
 }                                                                                                 \
-int SFX(k2ref_kogbet)(int32_t n, const R *A, R *U, R *V, R *S, int max_sweeps, double tol_factor, \
-                      int32_t *sweeps, int32_t *info)                                             \
+static int SFX(kogbet_impl)(int32_t n, const R *A, R *U, R *V, R *S, int max_sweeps,              \
+                            double tol_factor, int32_t *sweeps, int32_t *info, int dyn)           \
 {                                                                                                 \
     if (n < 1) return -1;                                                                         \
     size_t nn = (size_t)n * n;                                                                    \
@@ -80,10 +116,12 @@ int SFX(k2ref_kogbet)(int32_t n, const R *A, R *U, R *V, R *S, int max_sweeps, d
     while (!(off < tol) && sw < max_sweeps && off > 0) {                                          \
         for (int st = 0; st < n; ++st) {                                                          \
             int np = 0;                                                                           \
-            for (int i = 0; i < n; ++i) {                                                         \
-                int j = (st - i + n) % n;                                                         \
-                if (i < j) { pi[np] = i; pj[np] = j; ++np; }                                      \
-            }                                                                                     \
+            if (dyn) np = SFX(k2ref_dyn_pairs)(n, G, pi, pj);                                     \
+            else                                                                                  \
+                for (int i = 0; i < n; ++i) {                                                     \
+                    int j = (st - i + n) % n;                                                     \
+                    if (i < j) { pi[np] = i; pj[np] = j; ++np; }                                  \
+                }                                                                                 \
             for (int p = 0; p < np; ++p) {                                                        \
                 int i = pi[p], j = pj[p];                                                         \
                 PIVOT(G[(size_t)i * n + i], G[(size_t)i * n + j], G[(size_t)j * n + i],           \
@@ -136,6 +174,16 @@ int SFX(k2ref_kogbet)(int32_t n, const R *A, R *U, R *V, R *S, int max_sweeps, d
     for (int q = 0; q < n; ++q) memcpy(&V[(size_t)q * n], &T[(size_t)perm[q] * n], sizeof(R) * (size_t)n); \
     free(T); free(G); free(pi); free(pj); free(pu); free(pv); free(ps); free(perm);               \
     return 0;                                                                                     \
+}                                                                                                 \
+int SFX(k2ref_kogbet)(int32_t n, const R *A, R *U, R *V, R *S, int max_sweeps, double tol_factor, \
+                      int32_t *sweeps, int32_t *info)                                             \
+{                                                                                                 \
+    return SFX(kogbet_impl)(n, A, U, V, S, max_sweeps, tol_factor, sweeps, info, 0);              \
+}                                                                                                 \
+int SFX(k2ref_kogbet_dyn)(int32_t n, const R *A, R *U, R *V, R *S, int max_sweeps,                \
+                          double tol_factor, int32_t *sweeps, int32_t *info)                      \
+{                                                                                                 \
+    return SFX(kogbet_impl)(n, A, U, V, S, max_sweeps, tol_factor, sweeps, info, 1);              \
 }
 
 /* dA = U diag(dS) V^T: element (r, c) accumulates (U_rq dS_q) V_cq over q = 0..n-1 with fma. */

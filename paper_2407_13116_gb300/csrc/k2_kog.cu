@@ -23,6 +23,11 @@
 //
 // Per-step form (K2SVD_KOG_PLAIN): G in the workspace, three launches per step over the
 // whole batch, and a host read-back per sweep for the convergence test.
+//
+// Dynamic ordering (K2SVD_KOG_DYNAMIC, persistent form only): the pairs of a step are not
+// the modulus strategy's but the greedy choice by decreasing weight w_ij = g_ji^2 + g_ij^2
+// (Sect. 1 names the dynamic ordering as a candidate strategy); a step is then weights,
+// selection, pivot SVDs and rotations one after the other (kog_dynamic).
 #include <algorithm>
 #include <climits>
 #include <cstdint>
@@ -51,10 +56,11 @@ template <typename T> struct kog_params {
     const T *A;
     T *U, *V, *S;
     int32_t *sweeps, *info;
-    T *gws;                // G scratch base
+    T *gws;                // scratch base: G outside shared memory, pair weights
     int max_sweeps;
     double tol_factor;
     int nmax;              // largest order of the launch (shared-memory capacity)
+    int wsm;               // dynamic ordering: the pair weights in shared memory (else after G)
 };
 
 // pivot parameters of one step: 10 values for each of at most nmax/2 pivots, stored by
@@ -344,6 +350,262 @@ __global__ void __launch_bounds__(512) kog_persistent(const kog_params<T> P)
 }
 
 // ---------------------------------------------------------------------------------------
+// dynamic ordering: persistent kernel
+// ---------------------------------------------------------------------------------------
+// The greedy choice (scan the pairs by decreasing rank, take each whose indices are free)
+// is computed as a matching of locally dominant pairs: in rounds, every free index finds its
+// best free partner, and each pair of indices that are each other's best is taken.  Under a
+// strict total order of the pairs (weight, then pair index) both give the same pairs -- the
+// best remaining pair is always mutually best, and a mutually best pair is never beaten
+// later by a pair sharing one of its indices -- while the rounds here are few (every round
+// takes at least the best remaining pair) and each touches only the indices whose partner
+// was just taken.
+//
+// Step k: (A) all threads rotate G with the pivots of step k (G becomes G_{k+1}); (B) while
+// the last warps update U and V with step k's rotations, the first warps compute the
+// weights of G_{k+1}, choose the pairs of step k+1 and run their pivot SVDs into the other
+// buffer, so that the serial 2x2 SVDs hide behind the U and V work.
+//
+// Shared memory: G (unless GG), two buffers of pivot parameters, colsum (nmax), then ints:
+// perm and flip (2 nmax, for kog_finish), two buffers of pairs pi, pj (nmax/2 + 1 each) and
+// groups gi, gj (nmax each), used and best (nmax each), and four counters; then the
+// n(n-1)/2 pair weights when they fit (P.wsm; in the workspace otherwise).  Rescanning a
+// row of weights from global memory cost an L2 round trip per element: with the weights
+// in global memory the selection took 80% of a step at order 128.
+template <typename T>
+__host__ __device__ inline size_t kog_dyn_ints_end(int nmax, bool gg)        // bytes up to the weights
+{
+    const size_t g = gg ? 0 : (size_t)(nmax + 1) * nmax * sizeof(T);
+    const size_t ints = 2 * (size_t)nmax + 2 * (2 * (size_t)(nmax / 2 + 1) + 2 * (size_t)nmax) + 2 * (size_t)nmax + 8;
+    return (g + (2 * kog_piv_elems<T>(nmax) + (size_t)nmax) * sizeof(T) + ints * sizeof(int) + 15) & ~(size_t)15;
+}
+template <typename T>
+__host__ __device__ inline size_t kog_dyn_smem_bytes(int nmax, bool gg, bool wsm)
+{
+    return kog_dyn_ints_end<T>(nmax, gg) + (wsm ? (size_t)nmax * (nmax - 1) / 2 * sizeof(T) : 0) + 64;
+}
+
+// Packed index of the pair i < j: the pairs in lexicographic order (i, j).
+__device__ __forceinline__ int dyn_tri(int n, int i, int j) { return i * (2 * n - i - 1) / 2 + (j - i - 1); }
+
+// (w1, k1) ranks before (w2, k2): larger weight, then smaller pair index; k < 0 is no pair.
+// The weights are sums of squares (never negative, zero only as +0), so their bit patterns
+// order like their values: the comparisons run on the integer pipe, not the FP64 one.
+__device__ __forceinline__ uint64_t dyn_key(double w) { return dbits(w); }
+__device__ __forceinline__ uint64_t dyn_key(float w) { return fbits(w); }
+template <typename T> __device__ __forceinline__ bool dyn_before(T w1, int k1, T w2, int k2)
+{
+    if (k1 < 0) return false;
+    if (k2 < 0) return true;
+    const uint64_t a = dyn_key(w1), b = dyn_key(w2);
+    return a > b || (a == b && k1 < k2);
+}
+
+// Barrier over the nthreads first threads of the block (id 0 with all threads: __syncthreads).
+__device__ __forceinline__ void dyn_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+struct dyn_bufs {                      // one step's pairs and groups
+    int *pi, *pj, *gi, *gj;
+    int *np, *nq;                      // counters in shared memory
+};
+
+// Weights of G, the pairs of the next step and their pivot SVDs, by threads t0 = tid <
+// tn (the first tn threads of the block, synchronized on barrier `bar`).
+template <typename T>
+__device__ void dyn_select(const T *G, int ld, int n, T *W, int *used, int *best, dyn_bufs b, T *piv, int ps,
+                           int tid, int tn, int bar)
+{
+    for (int t = tid; t < (n + 1) / 2; t += tn)               // rows t and n-1-t: n-1 pairs a thread
+        for (int pass = 0; pass < 2; ++pass) {
+            const int i = pass ? n - 1 - t : t;
+            if (pass && i == t) break;
+            for (int j = i + 1; j < n; ++j) {
+                const T gij = G[(size_t)j * ld + i], gji = G[(size_t)i * ld + j];
+                W[dyn_tri(n, i, j)] = fma(gji, gji, gij * gij);
+            }
+        }
+    for (int q = tid; q < n; q += tn) { used[q] = 0; best[q] = -2; }
+    if (tid == 0) { *b.np = 0; *b.nq = 0; }
+    dyn_sync(bar, tn);
+    int taken = 0;
+    for (;;) {
+        for (int i = tid; i < n; i += tn) {
+            if (used[i] || (best[i] >= 0 && !used[best[i]])) continue;     // best partner still free
+            T bw = T(0); int bk = -1, bj = -1;
+            for (int j = 0; j < n; ++j) {
+                if (j == i || used[j]) continue;
+                const int k = i < j ? dyn_tri(n, i, j) : dyn_tri(n, j, i);
+                const T w = W[k];
+                if (dyn_before(w, k, bw, bk)) { bw = w; bk = k; bj = j; }
+            }
+            best[i] = bj;
+        }
+        dyn_sync(bar, tn);
+        for (int i = tid; i < n; i += tn) {
+            const int j = best[i];
+            if (!used[i] && j > i && best[j] == i) {           // mutually best: taken
+                const int a = atomicAdd(b.np, 1);
+                b.pi[a] = i; b.pj[a] = j;
+                used[i] = 1; used[j] = 1;
+            }
+        }
+        dyn_sync(bar, tn);
+        const int now = *b.np;
+        if (now == taken) break;                               // no free pair left
+        taken = now;
+    }
+    const int np = taken;
+    for (int a = tid; a < np; a += tn) { b.gi[a] = b.pi[a]; b.gj[a] = b.pj[a]; }
+    for (int q = tid; q < n; q += tn)
+        if (!used[q]) { const int a = np + atomicAdd(b.nq, 1); b.gi[a] = q; b.gj[a] = -1; }
+    for (int a = tid; a < np; a += tn) {
+        const int i = b.pi[a], j = b.pj[a];
+        kog_pivot(G[(size_t)i * ld + i], G[(size_t)i * ld + j], G[(size_t)j * ld + i], G[(size_t)j * ld + j], piv + a, ps);
+    }
+}
+
+// G <- U-hat^T G V-hat by 2x2 blocks of groups (as kog_rotate_g)
+template <typename T>
+__device__ __forceinline__ void dyn_rotate_g(T *G, int ld, int n, const dyn_bufs &b, int np, const T *piv, int ps,
+                                             int t0, int tn)
+{
+    const int nq = n - np;
+    for (int w2 = t0; w2 < nq * nq; w2 += tn) {
+        const int a = w2 % nq, bb = w2 / nq;
+        const int ia = b.gi[a], ja = b.gj[a], ib = b.gi[bb], jb = b.gj[bb];
+        if (ja < 0 && jb < 0) continue;
+        if (a == bb) {
+            G[(size_t)ia * ld + ia] = piv[8 * ps + a];
+            G[(size_t)ia * ld + ja] = T(0);
+            G[(size_t)ja * ld + ia] = T(0);
+            G[(size_t)ja * ld + ja] = piv[9 * ps + a];
+            continue;
+        }
+        T *c0 = G + (size_t)ib * ld, *c1 = jb >= 0 ? G + (size_t)jb * ld : nullptr;
+        T x00 = c0[ia], x10 = T(0), x01 = T(0), x11 = T(0);
+        if (ja >= 0) x10 = c0[ja];
+        if (jb >= 0) { x01 = c1[ia]; if (ja >= 0) x11 = c1[ja]; }
+        if (ja >= 0) {
+            rot2(x00, x10, piv + a, ps);
+            if (jb >= 0) rot2(x01, x11, piv + a, ps);
+        }
+        if (jb >= 0) {
+            rot2(x00, x01, piv + 4 * ps + bb, ps);
+            if (ja >= 0) rot2(x10, x11, piv + 4 * ps + bb, ps);
+        }
+        c0[ia] = x00;
+        if (ja >= 0) c0[ja] = x10;
+        if (jb >= 0) { c1[ia] = x01; if (ja >= 0) c1[ja] = x11; }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void dyn_rotate_uv(T *U, T *V, int n, const dyn_bufs &b, int np, const T *piv, int ps,
+                                              int t0, int tn)
+{
+    for (int w2 = t0; w2 < np * n; w2 += tn) {
+        const int r = w2 % n, a = w2 / n;
+        const int i = b.pi[a], j = b.pj[a];
+        rot2(U[(size_t)i * n + r], U[(size_t)j * n + r], piv + a, ps);
+        rot2(V[(size_t)i * n + r], V[(size_t)j * n + r], piv + 4 * ps + a, ps);
+    }
+}
+
+template <typename T, bool GG>
+__global__ void __launch_bounds__(512) kog_dynamic(const kog_params<T> P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ kog_sh sh;
+    const int nmax = P.nmax, ps = kog_piv_stride(nmax), h = nmax / 2 + 1;
+    T *Gs = reinterpret_cast<T *>(smem);
+    T *pivb[2];
+    pivb[0] = Gs + (GG ? 0 : (size_t)(nmax + 1) * nmax);
+    pivb[1] = pivb[0] + kog_piv_elems<T>(nmax);
+    T *colsum = pivb[1] + kog_piv_elems<T>(nmax);
+    int *perm = reinterpret_cast<int *>(colsum + nmax);
+    int *ip = perm + 2 * nmax;
+    dyn_bufs bufs[2];
+    for (int q = 0; q < 2; ++q) {
+        bufs[q].pi = ip; bufs[q].pj = ip + h; bufs[q].gi = ip + 2 * h; bufs[q].gj = ip + 2 * h + nmax;
+        ip += 2 * h + 2 * nmax;
+    }
+    int *used = ip, *best = ip + nmax, *cnt = ip + 2 * nmax;
+    bufs[0].np = cnt; bufs[0].nq = cnt + 1; bufs[1].np = cnt + 2; bufs[1].nq = cnt + 3;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (;;) {
+        if (tid == 0) sh.slot = atomicAdd(P.queue, 1);
+        __syncthreads();
+        const int slot = sh.slot;
+        __syncthreads();
+        if (slot >= P.count) break;
+        const kog_desc d = P.desc[slot];
+        const int n = d.n, ld = GG ? n : n + 1;
+        T *G = GG ? P.gws + d.goff : Gs;
+        T *U = P.U + d.off, *V = P.V + d.off, *S = P.S + d.soff;
+        T *W = P.wsm ? reinterpret_cast<T *>(smem + kog_dyn_ints_end<T>(nmax, GG))                 // pair weights
+                     : P.gws + d.goff + (GG ? (((int64_t)n * n + 1) & ~(int64_t)1) : 0);
+        const int k = kog_load(P.A + d.off, G, ld, U, V, n, &sh);
+        if (k == INT_MIN) {
+            kog_fail(U, V, S, n);
+            if (tid == 0) {
+                if (P.sweeps) P.sweeps[d.idx] = 0;
+                if (P.info) P.info[d.idx] = -1;
+            }
+            __syncthreads();
+            continue;
+        }
+        T *bc = reinterpret_cast<T *>(&sh.b);
+        const T nrm = kog_norm(G, n, ld, false, colsum, bc);
+        const T tol = (T(P.tol_factor) * T(n)) * kog_eps<T>::v() * nrm;
+        T off = kog_norm(G, n, ld, true, colsum, bc);
+        int sw = 0;
+        bool go = !(off < tol) && sw < P.max_sweeps && off > T(0);
+        // the selecting warps: enough for one thread per index, at most half the block
+        const int nw = (nt + 31) >> 5;
+        int w0 = (n + 31) >> 5;
+        if (w0 > nw / 2) w0 = nw / 2;
+        const bool split = w0 >= 1 && nt - 32 * w0 >= 32;
+        int cur = 0;
+        if (go) {
+            dyn_select(G, ld, n, W, used, best, bufs[0], pivb[0], ps, tid, nt, 0);
+            __syncthreads();
+        }
+        while (go) {
+            for (int st = 0; st < n; ++st) {
+                const int nxt = cur ^ 1;
+                const int np = *bufs[cur].np;
+                dyn_rotate_g(G, ld, n, bufs[cur], np, pivb[cur], ps, tid, nt);       // G_{k+1}
+                __syncthreads();
+                // the pairs of the next step (the first of the next sweep after the last
+                // one: unused when the sweeps end) beside the U and V updates of this one
+                if (split) {
+                    if (tid < 32 * w0) dyn_select(G, ld, n, W, used, best, bufs[nxt], pivb[nxt], ps, tid, 32 * w0, 1);
+                    else dyn_rotate_uv(U, V, n, bufs[cur], np, pivb[cur], ps, tid - 32 * w0, nt - 32 * w0);
+                } else {
+                    dyn_rotate_uv(U, V, n, bufs[cur], np, pivb[cur], ps, tid, nt);
+                    __syncthreads();
+                    dyn_select(G, ld, n, W, used, best, bufs[nxt], pivb[nxt], ps, tid, nt, 0);
+                }
+                __syncthreads();
+                cur = nxt;
+            }
+            ++sw;
+            off = kog_norm(G, n, ld, true, colsum, bc);
+            go = !(off < tol) && sw < P.max_sweeps && off > T(0);
+        }
+        kog_finish(G, ld, U, V, S, n, k, colsum, perm, G);
+        if (tid == 0) {
+            if (P.sweeps) P.sweeps[d.idx] = sw;
+            if (P.info) P.info[d.idx] = (off < tol || off == T(0)) ? 0 : 1;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // per-step form: state per matrix in the workspace
 // ---------------------------------------------------------------------------------------
 template <typename T> struct kog_state {
@@ -532,7 +794,7 @@ template <typename T> struct kog_plan {
     int bnmax[NBUCKETS];
     size_t off_desc, off_queue, off_g, off_state, off_piv, off_pivoff, total;
     std::vector<int64_t> pivoff;                     // per-step form
-    bool plain;
+    bool plain, dyn;
 };
 
 template <typename T>
@@ -541,6 +803,7 @@ static int make_plan(int64_t batch, const int32_t *n, const int64_t *offs, const
 {
     const int smax = kog_limits<T>::SMEM_MAX_N;
     pl.plain = (flags & K2SVD_KOG_PLAIN) != 0;
+    pl.dyn = (flags & K2SVD_KOG_DYNAMIC) != 0;
     pl.desc.resize((size_t)batch);
     for (int64_t i = 0; i < batch; ++i) {
         if (n[i] < 1 || n[i] > 4096) return -2;
@@ -560,12 +823,15 @@ static int make_plan(int64_t batch, const int32_t *n, const int64_t *offs, const
         pl.bnmax[b] = std::max(pl.bnmax[b], pl.desc[i].n);
     }
     for (int b = 1; b <= NBUCKETS; ++b) pl.bstart[b] = std::max(pl.bstart[b], pl.bstart[b - 1]);
-    // G scratch: every matrix in the per-step form, the global bucket in the persistent form
+    // scratch: G for every matrix in the per-step form and for the global bucket in the
+    // persistent form, then the n(n-1)/2 pair weights of every matrix with the dynamic ordering
     int64_t g = 0;
     for (auto &d : pl.desc) {
-        if (pl.plain || bucket_of(d.n, smax) == 4) {
+        const bool gg = pl.plain || bucket_of(d.n, smax) == 4;
+        if (gg || pl.dyn) {
             d.goff = g;
-            g += ((int64_t)d.n * d.n + 1) & ~(int64_t)1;
+            if (gg) g += ((int64_t)d.n * d.n + 1) & ~(int64_t)1;
+            if (pl.dyn) g += ((int64_t)d.n * (d.n - 1) / 2 + 1) & ~(int64_t)1;
         }
     }
     size_t off = 0;
@@ -588,28 +854,50 @@ static int make_plan(int64_t batch, const int32_t *n, const int64_t *offs, const
 }
 
 struct tune_key {
-    int dev, tsize, bucket;
-    bool operator<(const tune_key &o) const { return std::tie(dev, tsize, bucket) < std::tie(o.dev, o.tsize, o.bucket); }
+    int dev, tsize, bucket, dyn;
+    bool operator<(const tune_key &o) const
+    {
+        return std::tie(dev, tsize, bucket, dyn) < std::tie(o.dev, o.tsize, o.bucket, o.dyn);
+    }
 };
 static std::mutex g_mu;
 static std::map<tune_key, int> g_tuned;
 
 static int default_threads(int nmax) { return nmax <= 32 ? 64 : (nmax <= 64 ? 256 : 512); }
 
-template <typename T, bool GG>
-static cudaError_t launch_bucket(const kog_params<T> &P, int threads, cudaStream_t st, int *queue_dev)
+template <typename T, bool GG, bool DYN>
+static cudaError_t launch_bucket_k(const kog_params<T> &Pin, int threads, cudaStream_t st, int *queue_dev)
 {
+    kog_params<T> P = Pin;
+    auto kern = DYN ? kog_dynamic<T, GG> : kog_persistent<T, GG>;
     size_t smem = kog_smem_bytes<T>(P.nmax, GG);
-    cudaError_t e = cudaFuncSetAttribute(kog_persistent<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    P.wsm = 0;
+    if (DYN) {                                         // the weights in shared memory when they fit
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return cudaErrorUnknown;
+        P.wsm = (!GG && kog_dyn_smem_bytes<T>(P.nmax, GG, true) <= (size_t)optin) ? 1 : 0;
+        smem = kog_dyn_smem_bytes<T>(P.nmax, GG, P.wsm != 0);
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int blocks = 0;
-    if (grid_for(kog_persistent<T, GG>, threads, smem, &blocks) != 0) return cudaErrorUnknown;
+    if (grid_for(kern, threads, smem, &blocks) != 0) return cudaErrorUnknown;
     if (blocks > P.count) blocks = P.count;
     if (blocks < 1) return cudaSuccess;
     e = cudaMemsetAsync(queue_dev, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    kog_persistent<T, GG><<<blocks, threads, smem, st>>>(P);
+    kern<<<blocks, threads, smem, st>>>(P);
     return cudaPeekAtLastError();
+}
+
+template <typename T>
+static cudaError_t launch_bucket(const kog_params<T> &P, int bucket, bool dyn, int threads, cudaStream_t st, int *queue_dev)
+{
+    if (bucket == 4)
+        return dyn ? launch_bucket_k<T, true, true>(P, threads, st, queue_dev) : launch_bucket_k<T, true, false>(P, threads, st, queue_dev);
+    return dyn ? launch_bucket_k<T, false, true>(P, threads, st, queue_dev) : launch_bucket_k<T, false, false>(P, threads, st, queue_dev);
 }
 
 template <typename T>
@@ -626,8 +914,7 @@ static cudaError_t launch_persistent(const kog_plan<T> &pl, kog_params<T> base, 
         P.count = cnt;
         P.queue = queues + 16 * b;
         P.nmax = pl.bnmax[b];
-        cudaError_t e = (b == 4) ? launch_bucket<T, true>(P, threads[b], st, P.queue)
-                                 : launch_bucket<T, false>(P, threads[b], st, P.queue);
+        cudaError_t e = launch_bucket<T>(P, b, pl.dyn, threads[b], st, P.queue);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -645,7 +932,7 @@ static int autotune(const kog_plan<T> &pl, const kog_params<T> &base, cudaStream
         int cnt = pl.bstart[b + 1] - pl.bstart[b];
         threads[b] = default_threads(pl.bnmax[b]);
         if (cnt <= 0) continue;
-        tune_key key{dev, (int)sizeof(T), b};
+        tune_key key{dev, (int)sizeof(T), b, pl.dyn ? 1 : 0};
         {
             std::lock_guard<std::mutex> lk(g_mu);
             auto it = g_tuned.find(key);
@@ -665,7 +952,7 @@ static int autotune(const kog_plan<T> &pl, const kog_params<T> &base, cudaStream
         for (int t : cand) {
             if (t < 32) continue;
             cudaEventRecord(e0, st);
-            cudaError_t e = (b == 4) ? launch_bucket<T, true>(P, t, st, P.queue) : launch_bucket<T, false>(P, t, st, P.queue);
+            cudaError_t e = launch_bucket<T>(P, b, pl.dyn, t, st, P.queue);
             cudaEventRecord(e1, st);
             if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
                 cudaEventDestroy(e0); cudaEventDestroy(e1);
@@ -757,8 +1044,8 @@ static int kogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
     if (!S) return -8;
     if (max_sweeps < 0) return -11;
     if (!(tol_factor > 0)) return -12;
-    if (flags & ~(K2SVD_KOG_PLAIN | K2SVD_KOG_GRAPH | K2SVD_KOG_NOTUNE)) return -13;
-    if ((flags & K2SVD_KOG_PLAIN) && (flags & K2SVD_KOG_GRAPH)) return -13;
+    if (flags & ~(K2SVD_KOG_PLAIN | K2SVD_KOG_GRAPH | K2SVD_KOG_NOTUNE | K2SVD_KOG_DYNAMIC)) return -13;
+    if ((flags & K2SVD_KOG_PLAIN) && (flags & (K2SVD_KOG_GRAPH | K2SVD_KOG_DYNAMIC))) return -13;
     if (!workspace || ((uintptr_t)workspace & 255)) return -14;
     kog_plan<T> pl;
     int rc = make_plan<T>(batch, n, offs, soffs, flags, pl);
@@ -790,7 +1077,7 @@ static int kogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
     graph_key key;
     key.sig = {dev, (int64_t)sizeof(T), batch, (int64_t)(uintptr_t)A, (int64_t)(uintptr_t)U, (int64_t)(uintptr_t)V,
                (int64_t)(uintptr_t)S, (int64_t)(uintptr_t)sweeps, (int64_t)(uintptr_t)info, max_sweeps,
-               (int64_t)(uintptr_t)workspace};
+               (int64_t)(uintptr_t)workspace, flags};
     int64_t tbits;
     std::memcpy(&tbits, &tol_factor, sizeof tbits);
     key.sig.push_back(tbits);
@@ -933,6 +1220,7 @@ static int kogbet_noalloc(int64_t batch, const int32_t *n, const int64_t *offs, 
     pl.off_desc = align256(128 * sizeof(int));
     pl.off_g = pl.off_desc + align256((size_t)batch * sizeof(kog_desc));
     pl.plain = false;
+    pl.dyn = false;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *ws = static_cast<unsigned char *>(scratch);
     if (cudaMemcpyAsync(ws + pl.off_desc, desc, (size_t)batch * sizeof(kog_desc), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -948,7 +1236,7 @@ static int kogbet_noalloc(int64_t batch, const int32_t *n, const int64_t *offs, 
     for (int b = 0; b < NBUCKETS; ++b) {             // tuned block sizes if known, else defaults
         threads[b] = default_threads(pl.bnmax[b]);
         std::lock_guard<std::mutex> lk2(g_mu);
-        auto it = g_tuned.find(tune_key{dev, (int)sizeof(double), b});
+        auto it = g_tuned.find(tune_key{dev, (int)sizeof(double), b, 0});
         if (it != g_tuned.end()) threads[b] = it->second;
     }
     return launch_persistent<double>(pl, base, threads, st, ws) == cudaSuccess ? 0 : K2SVD_ECUDA;

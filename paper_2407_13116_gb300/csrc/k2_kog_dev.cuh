@@ -13,7 +13,8 @@ namespace k2 {
 struct kog_desc {
     int32_t n, idx;       // order, index in the caller's batch
     int64_t off, soff;    // element offsets of A/U/V and of S
-    int64_t goff;         // element offset of this matrix's G in the workspace scratch
+    int64_t goff;         // element offset of this matrix's scratch in the workspace: G when
+                          // it is not in shared memory, then (dynamic ordering) the weights
 };
 
 // Pair p of step k of the modulus strategy: the pairs i < j with i + j = k (mod n), in

@@ -363,7 +363,7 @@ def from_planes(X, shape):
 # ------------------------------------------------------------------------------------------
 # batched n x n Kogbetliantz SVD
 # ------------------------------------------------------------------------------------------
-KOG_PLAIN, KOG_GRAPH, KOG_NOTUNE = 1, 2, 4
+KOG_PLAIN, KOG_GRAPH, KOG_NOTUNE, KOG_DYNAMIC = 1, 2, 4, 8
 
 
 def kog_layout(orders):
@@ -408,7 +408,8 @@ def kogbet(A, orders, max_sweeps=40, tol_factor=1.0, flags=0, workspace=None, U=
            sweeps=None, info=None):
     """SVD of the packed batch A (flat, column-major per matrix, orders[i] each) by the
     persistent Kogbetliantz driver (flags: KOG_PLAIN for the per-step form, KOG_GRAPH to
-    launch through a cached CUDA graph).  Returns (U, S, V, sweeps, info) packed like A."""
+    launch through a cached CUDA graph, KOG_DYNAMIC for the dynamic pivot ordering).
+    Returns (U, S, V, sweeps, info) packed like A."""
     p = _prefix(A.dtype)
     dev = A.device
     n, offs, soffs, tot, stot = kog_layout(orders)

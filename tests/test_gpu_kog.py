@@ -32,10 +32,10 @@ def _gpu(flat, orders, flags=0, max_sweeps=40):
     return U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy(), sw.cpu().numpy(), info.cpu().numpy()
 
 
-def _oracle(mats, prec, max_sweeps=40):
+def _oracle(mats, prec, max_sweeps=40, dynamic=False):
     U, S, V, sw, info = [], [], [], [], []
     for m in mats:
-        u, s, v, a, b = oracle.kogbet(m, prec, max_sweeps=max_sweeps)
+        u, s, v, a, b = oracle.kogbet(m, prec, max_sweeps=max_sweeps, dynamic=dynamic)
         U.append(u.T.reshape(-1)); V.append(v.T.reshape(-1)); S.append(s); sw.append(a); info.append(b)
     return np.concatenate(U), np.concatenate(S), np.concatenate(V), np.array(sw), np.array(info)
 
@@ -69,6 +69,31 @@ def test_parity_all_buckets_and_forms(prec, flags):
     ref = _oracle(mats, prec)
     _same(got, ref, "kogbet %s flags=%d" % (prec, flags))
     assert (got[4] == 0).all()
+
+
+@pytest.mark.parametrize("prec", ["d", "s"])
+@pytest.mark.parametrize("flags", [8, 8 | 2, 8 | 4])
+def test_dynamic_ordering_parity(prec, flags):
+    """The dynamic ordering (K2SVD_KOG_DYNAMIC) in every bucket, plain persistent, graph and
+    untuned, bit for bit against the oracle's dynamic ordering."""
+    orders = ORDERS_D if prec == "d" else ORDERS_S
+    flat, mats = _batch(orders, 41 + flags, prec, smin=1e-12 if prec == "d" else 1e-5)
+    got = _gpu(flat, orders, flags)
+    ref = _oracle(mats, prec, dynamic=True)
+    _same(got, ref, "kogbet dynamic %s flags=%d" % (prec, flags))
+    assert (got[4] == 0).all()
+
+
+def test_dynamic_ordering_max_sweeps_and_errors():
+    orders = [40, 9, 128]
+    flat, mats = _batch(orders, 51, "d")
+    got = _gpu(flat, orders, 8, max_sweeps=2)
+    ref = _oracle(mats, "d", max_sweeps=2, dynamic=True)
+    _same(got, ref, "dynamic max_sweeps=2")
+    assert (got[3] == 2).all() and (got[4] == 1).all()
+    A = torch.from_numpy(flat).to(DEV)
+    with pytest.raises(k2().K2SVDError, match="-13"):
+        k2().kogbet(A, orders, flags=8 | 1)
 
 
 def test_graph_replay_and_reuse():
