@@ -688,7 +688,8 @@ def e2e_leg(steps, warmup, dev, D):
     return {"value": D.world * 2 * n / el, "unit": "SVDs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "batch": 2 * n, "ms_per_step": el * 1e3, "streams": NS, "chunk": c, "link": link,
             "copy_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6,
-            "step_ms_min_max": [min(per) * 1e3, max(per) * 1e3]}
+            "step_ms_min_max": [min(per) * 1e3, max(per) * 1e3],
+            "step_ms_median": statistics.median(per) * 1e3}
 
 
 def cpu_baseline(seconds=10.0):
@@ -785,7 +786,7 @@ def run_ours(a):
     if not a.no_kog:
         out["kogbet"] = kog_leg(max(2, a.steps // 3), 1, dev, D)
     if D.world == 1 and not a.no_e2e:
-        out["e2e"] = e2e_leg(max(2, a.steps // 3), 1, dev, D)
+        out["e2e"] = e2e_leg(max(5, a.steps // 2), 1, dev, D)
     if D.rank == 0 and D.world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     D.close()
