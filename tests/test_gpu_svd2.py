@@ -133,8 +133,9 @@ def test_small_and_ragged_batches(n):
     _assert_same(_gpu_ge(G, "d"), oracle.gesvd2(G, "d"), "n=%d" % n)
 
 
-def test_strided_planes_and_optional_outputs():
-    n, ld = 5000, 5123
+@pytest.mark.parametrize("n", [5000, 70001])        # the fused kernel; the split FP64 path (>= 65536)
+def test_strided_planes_and_optional_outputs(n):
+    ld = n + 123
     G = I.general(n, 4100, "d", "narrow")
     Gt = torch.zeros((4, ld), dtype=torch.float64, device=DEV)
     Gt[:, :n] = torch.from_numpy(G).to(DEV)
@@ -154,6 +155,20 @@ def test_strided_planes_and_optional_outputs():
     assert np.array_equal(_u(V[:, :n].cpu().numpy()), _u(ref["V"]))
     assert np.array_equal(_u(S[:, :n].cpu().numpy()), _u(ref["S"]))
     assert (U[:, n:] == 7.0).all() and (S[:, n:] == 7.0).all()     # nothing written past n
+    # (e,f) outputs and info on strided planes too
+    Se = torch.full((2, ld + 1), 7, dtype=torch.int32, device=DEV)
+    Sf = torch.full((2, ld + 1), 7.0, dtype=torch.float64, device=DEV)
+    info = torch.full((n + 5,), 7, dtype=torch.int32, device=DEV)
+    rc = L.k2svd_dgesvd2(n, C.c_void_p(Gt.data_ptr()), ld, C.c_void_p(U.data_ptr()), ld + 7,
+                         C.c_void_p(V.data_ptr()), ld, C.c_void_p(S.data_ptr()), ld + 1, C.c_void_p(Se.data_ptr()),
+                         C.c_void_p(Sf.data_ptr()), C.c_void_p(info.data_ptr()),
+                         C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(Se[:, :n].cpu().numpy(), ref["Se"])
+    assert np.array_equal(_u(Sf[:, :n].cpu().numpy()), _u(ref["Sf"]))
+    assert np.array_equal(info[:n].cpu().numpy(), ref["info"])
+    assert (info[n:] == 7).all() and (Se[:, n:] == 7).all()
 
 
 def test_argument_errors():
