@@ -716,6 +716,15 @@ def cpu_baseline(seconds=10.0):
                       "OpenMP over matrices on %d host threads, %.1f s" % (m, m, cores, el)}
 
 
+def headline_config():
+    """The headline workload, shared by both arms (the reference arm times a sample of it)."""
+    return {"workload": "wide-range FP64 2x2 SVD: 2^27 general (k2svd_dgesvd2) + 2^27 upper-triangular "
+                        "(k2svd_dtrsvd2) per GPU, exponents uniform in [-1021,1021], 2% subnormal or "
+                        "near-overflow entries, SoA planes",
+            "matrices_per_gpu_per_step": 2 * N_HALF_D, "l2": "inputs (7.5 GB) larger than L2",
+            "parallelism": "one slice of the global batch per rank (weak scaling, no collective)"}
+
+
 def run_ours(a):
     import torch
     D = Dist()
@@ -753,11 +762,7 @@ def run_ours(a):
     out = {"metric": METRIC, "value": value, "unit": "SVDs/s", "n_gpus": D.world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "wide-range FP64 2x2 SVD: 2^27 general (k2svd_dgesvd2) + 2^27 upper-triangular "
-                                  "(k2svd_dtrsvd2) per GPU, exponents uniform in [-1021,1021], 2% subnormal or "
-                                  "near-overflow entries, SoA planes",
-                      "matrices_per_gpu_per_step": 2 * N_HALF_D, "l2": "inputs (7.5 GB) larger than L2",
-                      "parallelism": "one slice of the global batch per rank (weak scaling, no collective)"},
+           "config": headline_config(),
            "clocks": res["clocks"], "gpu_launches": res["launches"], "roofline": roofline,
            "pipe_rates": rates}
     if not a.no_fp32:
@@ -822,12 +827,12 @@ def run_reference(a):
         ts.append(time.perf_counter() - t)
     el = statistics.mean(ts)
     value = 2 * m / el
-    sample = "first %d general + %d triangular matrices of the wide-range FP64 workload per step" % (m, m)
+    sample = ("first %d general + %d triangular matrices of the wide-range FP64 workload per step, by the "
+              "oracle (plain C, OpenMP over matrices on the host cores)" % (m, m))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "SVDs/s", "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": el * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "wide-range FP64 2x2 SVD (oracle, plain C on the host cores)",
-                      "matrices_per_step": 2 * m, "parallelism": "OpenMP over matrices"},
+           "config": headline_config(),
            "cpu_baseline": {"value": value, "unit": "SVDs/s", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "SVDs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
