@@ -1060,7 +1060,7 @@ static int kogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
     base.desc = nullptr; base.count = 0; base.queue = nullptr;
     base.A = A; base.U = U; base.V = V; base.S = S; base.sweeps = sweeps; base.info = info;
     base.gws = reinterpret_cast<T *>(ws + pl.off_g);
-    base.max_sweeps = max_sweeps; base.tol_factor = tol_factor; base.nmax = 0;
+    base.max_sweeps = max_sweeps; base.tol_factor = tol_factor; base.nmax = 0; base.wsm = 0;
     if (pl.plain) {
         if (batch > 65535) return -1;                  // one grid row per matrix
         return kogbet_plain<T>(pl, base, st, ws);
@@ -1229,7 +1229,7 @@ static int kogbet_noalloc(int64_t batch, const int32_t *n, const int64_t *offs, 
     base.desc = nullptr; base.count = 0; base.queue = nullptr;
     base.A = A; base.U = U; base.V = V; base.S = S; base.sweeps = sweeps; base.info = info;
     base.gws = reinterpret_cast<double *>(ws + pl.off_g);
-    base.max_sweeps = max_sweeps; base.tol_factor = tol_factor; base.nmax = 0;
+    base.max_sweeps = max_sweeps; base.tol_factor = tol_factor; base.nmax = 0; base.wsm = 0;
     int dev;
     if (cudaGetDevice(&dev) != cudaSuccess) return K2SVD_ECUDA;
     int threads[NBUCKETS];
