@@ -31,3 +31,18 @@ def test_library_exports_every_declared_symbol():
     missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
     assert not missing, missing
     assert lib.k2svd_version() == 100
+
+
+def test_headers_compile_as_c99_and_cpp(tmp_path):
+    """The public headers are plain C: they compile as C99 (pedantic) and as C++."""
+    import shutil
+    import subprocess
+    inc = os.path.join(ROOT, "include")
+    for cc, std, name in (("gcc", "-std=c99", "h.c"), ("g++", "-std=c++11", "h.cpp")):
+        if not shutil.which(cc):
+            continue
+        src = tmp_path / name
+        src.write_text('#include "k2svd.h"\n#include "k2probe.h"\nint main(void) { return 0; }\n')
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I" + inc, "-fsyntax-only", str(src)],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
