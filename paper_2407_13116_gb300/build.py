@@ -1,9 +1,11 @@
-"""Build libk2svd.so in-tree with nvcc for sm_103a.
+"""Build libk2svd.so and libk2probe.so in-tree with nvcc for sm_103a.
 
-Each .cu file under csrc/ is compiled in parallel into csrc/_build/*.o and linked into
-csrc/libk2svd.so.  The numerics flags keep IEEE semantics: no flush to zero, correctly
-rounded division and square root, and no contraction of a*b+c into an fma (the paper's
-formulas call fma explicitly where they want one).
+Each .cu file under csrc/ is compiled in parallel into csrc/_build/*.o.  The method's
+sources are linked into csrc/libk2svd.so (include/k2svd.h); the measurement probes
+(k2_probe.cu, include/k2probe.h) into a library of their own, csrc/libk2probe.so, so the
+product library holds no measurement code.  The numerics flags keep IEEE semantics: no
+flush to zero, correctly rounded division and square root, and no contraction of a*b+c
+into an fma (the paper's formulas call fma explicitly where they want one).
 """
 import concurrent.futures as cf
 import glob
@@ -15,6 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(CSRC, "_build")
 LIB = os.path.join(CSRC, "libk2svd.so")
+PROBE_LIB = os.path.join(CSRC, "libk2probe.so")
+PROBE_SRC = "k2_probe.cu"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NUMERICS = ["-ftz=false", "-prec-div=true", "-prec-sqrt=true", "--fmad=false"]
@@ -34,14 +38,15 @@ def _deps():
 
 
 def _stale():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
 def build(force=False, verbose=False):
-    """Compile every CUDA source and link libk2svd.so; returns its path."""
+    """Compile every CUDA source and link libk2svd.so and libk2probe.so; returns the
+    path of libk2svd.so."""
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
@@ -60,14 +65,16 @@ def build(force=False, verbose=False):
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(one, srcs))
-    tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
+    probe = [o for o, s in zip(objs, srcs) if os.path.basename(s) == PROBE_SRC]
+    method = [o for o, s in zip(objs, srcs) if os.path.basename(s) != PROBE_SRC]
+    for out, parts in ((LIB, method), (PROBE_LIB, probe)):
+        tmp = out + ".tmp.%d" % os.getpid()
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + parts + ["-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
+        os.replace(tmp, out)
     return LIB
-
 
 if __name__ == "__main__":
     print(build(force=True, verbose=True))

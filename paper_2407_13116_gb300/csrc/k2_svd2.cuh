@@ -171,16 +171,36 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
     ef<T> era = ef_of(ra), erb = ef_of(rb), erc = ef_of(rc);
     T t2;
     bool t2inf = false;
+    // The cases of Alg. 1 only choose the operands of one division: the plain quotient
+    // 2 r~22 / r~12 of eq. (t2f''), or the (e,f) quotient (2 r~12 r~22) / Y of eqs. (t2f''')
+    // and (t2f') with Y = r~11^2 or (h - r~22)(h + r~22).  One call site, so that a warp
+    // whose lanes take different cases divides once.
+    int kind = -1;                                         // 0: plain; 1: (e,f); 2: t2 = inf
+    ef<T> Y;
+    Y.e = 0; Y.f = T(1);
     if (pos_eq(ra, rc)) {                                        // eq. (t2f'')
-        t2 = qdiv(T(2) * rc, rb);
+        kind = 0;
         flags |= FL_T2F2;
     } else if (pos_eq(rb, rc)) {                                 // eq. (t2f''')
-        t2 = ef_fl(ef_div(ef_mul(ef_pow2(1, erb), erc), ef_mul(era, era)));
+        kind = 1; Y = ef_mul(era, era);
         flags |= FL_T2F3;
     } else if (pos_lt(qdiv(ra, rb), fpt<T>::eps())) {                 // eq. (t2f''), only for t' ~ 13
-        t2 = qdiv(T(2) * rc, rb);
+        kind = 0;
         flags |= FL_T2F2;
-    } else if (NCR) {                                      // Alg. 1: tan(2 phi) without squaring
+    } else if (!NCR) {                                     // eq. (t2f')
+        T h = hypot_cr(ra, rb);
+        if (pos_eq(h, rc)) kind = 2;
+        else { kind = 1; Y = ef_mul(ef_minus(h, rc), ef_plus(h, rc)); }
+    }
+    if (kind >= 0) {
+        if (kind == 2) { t2 = T(0); t2inf = true; }
+        else {
+            const ef<T> X = ef_mul(ef_pow2(1, erb), erc);
+            const T q = qdiv(kind == 0 ? T(2) * rc : X.f, kind == 0 ? rb : Y.f);
+            if (kind == 0) t2 = q;
+            else { ef<T> w; renorm(q, X.e - Y.e, w.e, w.f); t2 = ef_fl(w); }
+        }
+    } else {                                               // NCR: Alg. 1 without squaring
         T x, y, num;
         if (pos_lt(rb, ra)) { x = qdiv(rb, ra); y = qdiv(rc, ra); num = (T(2) * x) * y; }
         else { x = qdiv(ra, rb); y = qdiv(rc, rb); num = T(2) * y; }
@@ -188,13 +208,6 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
         if (!gt0(den)) den = T(0);                         // max(den, 0), -0 -> +0
         t2 = qdiv(num, den);
         flags |= FL_T2NCR;
-    } else {                                               // eq. (t2f')
-        T h = hypot_cr(ra, rb);
-        if (pos_eq(h, rc)) { t2 = T(0); t2inf = true; }
-        else {
-            ef<T> s = ef_plus(h, rc), d = ef_minus(h, rc);
-            t2 = ef_fl(ef_div(ef_mul(ef_pow2(1, erb), erc), ef_mul(d, s)));
-        }
     }
     if (is_inf(t2)) t2inf = true;
     T tf;
@@ -248,6 +261,26 @@ template <typename T> __device__ __forceinline__ m22<T> vcheck(const tri_out<T> 
     return m;
 }
 
+// eq. (QR15) with Thm. 3.5: r12 and r22 by fma, except the one with the essential
+// subtraction (r22 when g12''' and g22''' have equal signs, else r12), which comes from eq.
+// (EXT) when tan(theta) is inexact (Lemma 3.4); both divided by sec(theta).  Written with a
+// single call of each primitive, so that a warp whose lanes take different cases runs the
+// long eq. (EXT) body once, not once per case.  FDIV: see csdiv.
+template <typename T, bool FDIV>
+__device__ __forceinline__ void urv15_r(T g11, T g21, T g12, T g22, T tth, T secth, T &r12, T &r22, int &flags)
+{
+    T n12 = fma(g22, tth, g12);
+    T n22 = fma(ngt(g12), tth, g22);
+    if (!eq0(fma(tth, g11, ngt(g21)))) {                 // tan(theta) inexact: Thm. 3.5
+        const bool e22 = lt0(g12) == lt0(g22);
+        const T e = ext_num_div(e22 ? g22 : g12, g11, e22 ? g12 : g22, g21, e22, g11);
+        if (e22) n22 = e; else n12 = e;
+        flags |= FL_EXT;
+    }
+    r12 = csdiv<FDIV>(n12, secth);
+    r22 = csdiv<FDIV>(n22, secth);
+}
+
 // Phase 1 (Sect. 3.1, eqs. (eG), (s)): the type t of G, the prescaling exponent
 // s = e_nu - e_G - (scale type + extra) (class 9 is not scaled: s = 0), G <- 2^s G (exact
 // for s >= 0, one rounding per element otherwise), and the type t' of the scaled matrix.
@@ -283,8 +316,8 @@ template <typename T> struct svd2_mid {
 
 // Phases 1 and 2 (Sect. 3.1, 3.2).  Returns false when o is complete (the simple classes,
 // the fallback of Sect. 3.2.2), true when phase 3 (svd2_b) must finish from m.  FDIV: the
-// quotients of eq. (QR15) (tan theta, r12, r22) on the FP64 divider (see csdiv).
-template <typename T, bool NCR = false, bool FDIV = false>
+// quotients r12, r22 of eq. (QR15) on the FP64 divider, FDIV_T: tan theta (see csdiv).
+template <typename T, bool NCR = false, bool FDIV = false, bool FDIV_T = FDIV>
 __device__ __forceinline__ bool svd2_a(T g11, T g21, T g12, T g22, svd2_out<T> &o, svd2_mid<T> &m)
 {
     int t, s, tp, flags = 0;
@@ -322,21 +355,10 @@ __device__ __forceinline__ bool svd2_a(T g11, T g21, T g12, T g22, svd2_out<T> &
         const bool pu = pos_lt(g11, g21);
         if (pu) { T x = g11; g11 = g21; g21 = x; x = g12; g12 = g22; g22 = x; }
         // eq. (QR15)
-        const T tth = csdiv<FDIV>(g21, g11);
+        const T tth = csdiv<FDIV_T>(g21, g11);
         const T secth = hyp<NCR>(tth, T(1));
         T r11 = w1, r12, r22;
-        if (eq0(fma(tth, g11, ngt(g21)))) {                // tan(theta) exact: Lemma 3.4
-            r12 = csdiv<FDIV>(fma(g22, tth, g12), secth);
-            r22 = csdiv<FDIV>(fma(ngt(g12), tth, g22), secth);
-        } else if (lt0(g12) == lt0(g22)) {         // Thm. 3.5: r22 by eq. (EXT)
-            r12 = csdiv<FDIV>(fma(g22, tth, g12), secth);
-            r22 = csdiv<FDIV>(ext_num_div(g22, g11, g12, g21, true, g11), secth);
-            flags |= FL_EXT;
-        } else {                                           // Thm. 3.5: r12 by eq. (EXT)
-            r22 = csdiv<FDIV>(fma(ngt(g12), tth, g22), secth);
-            r12 = csdiv<FDIV>(ext_num_div(g12, g11, g22, g21, false, g11), secth);
-            flags |= FL_EXT;
-        }
+        urv15_r<T, FDIV>(g11, g21, g12, g22, tth, secth, r12, r22, flags);
         if (eq0(r12) || eq0(r22)) {
             // R'' of type 9 (or 1) or 5: finish as Sect. 3.1, G' = S1 P_U U_theta R'' P_V^T
             flags |= FL_FALLBACK;
@@ -484,18 +506,7 @@ __device__ __forceinline__ void svd2(T g11, T g21, T g12, T g22, svd2_out<T> &o)
         const T tth = qdiv(g21, g11);
         const T secth = hyp<NCR>(tth, T(1));
         T r11 = w1, r12, r22;
-        if (eq0(fma(tth, g11, ngt(g21)))) {                // tan(theta) exact: Lemma 3.4
-            r12 = qdiv(fma(g22, tth, g12), secth);
-            r22 = qdiv(fma(ngt(g12), tth, g22), secth);
-        } else if (lt0(g12) == lt0(g22)) {         // Thm. 3.5: r22 by eq. (EXT)
-            r12 = qdiv(fma(g22, tth, g12), secth);
-            r22 = qdiv(ext_num_div(g22, g11, g12, g21, true, g11), secth);
-            flags |= FL_EXT;
-        } else {                                           // Thm. 3.5: r12 by eq. (EXT)
-            r22 = qdiv(fma(ngt(g12), tth, g22), secth);
-            r12 = qdiv(ext_num_div(g12, g11, g22, g21, false, g11), secth);
-            flags |= FL_EXT;
-        }
+        urv15_r<T, false>(g11, g21, g12, g22, tth, secth, r12, r22, flags);
         if (eq0(r12) || eq0(r22)) {
             // R'' of type 9 (or 1) or 5: finish as Sect. 3.1, G' = S1 P_U U_theta R'' P_V^T
             flags |= FL_FALLBACK;

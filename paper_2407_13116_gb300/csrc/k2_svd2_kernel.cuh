@@ -7,7 +7,6 @@
 // persistent: (SM count) x (resident blocks per SM) blocks stride over the batch.
 #pragma once
 #include <cstdint>
-#include <mutex>
 #include <cuda_runtime.h>
 
 #include "k2_svd2.cuh"
@@ -106,161 +105,126 @@ static int launch(const svd_args<T> &a, cudaStream_t st)
 
 // ---------------------------------------------------------------------------------------
 // Split form of the FP64 general kernel: phases 1-2 (svd2a_kernel) and phase 3
-// (svd2b_kernel) as two launches, the state between them (R, tan and sec of theta, the
-// permutations and signs: svd2_mid) in a scratch buffer.  Same operations as the fused
-// kernel, so the same bits.  Each launch runs part of the method's code, and matrices of
-// classes 13 and 15 meet in one copy of Alg. 1 and 2 instead of diverging into two.
-// Each half also gets its own placement of the quotients (SPLIT_FDIV_*).  Measured on a
-// GB300 against the fused kernel: 22% faster on wide-range matrices (all of class 15), 32%
-// faster on narrow-range ones with triangular and zero-row inputs mixed in.  For float the
-// fused kernel stays faster (the split one took 1.38 times as long).
+// (svd2b_kernel) as two launches.  Same operations as the fused kernel, so the same bits.
+// Each launch runs part of the method's code, and matrices of classes 13 and 15 meet in one
+// copy of Alg. 1 and 2 instead of diverging into two.  Each half also gets its own
+// placement of the quotients (SPLIT_FDIV_*).
+//
+// No scratch memory: the state between the halves (R, tan and sec of theta, s, the
+// permutations and signs: svd2_mid, 48 bytes) is parked in the caller's output planes of the
+// same matrix -- u11, u21, u12, u22 <- r11, r12, r22, tan theta; v11 <- sec theta;
+// sigma1 <- a packed word with the sign bit set -- which phase 3 then overwrites with the
+// results.  A final sigma1 is never negative (+0 or above, or a positive NaN for a
+// non-finite input), so the sign bit of the sigma1 plane tells phase 3 which matrices are
+// still to finish.  Each half runs once over the whole batch.  Measured on a GB300 (2^27
+// wide-range matrices): chunks small enough for the parked state to stay in L2 between the
+// two launches (3 or 6 rounds of the persistent grid, 45 or 90 MB) took 41.1 and 39.9 ms
+// against 38.3 ms for large chunks: each launch's ramp-up and drain cost more than the
+// state's DRAM traffic saves (the kernels are bound by their pipes, not by DRAM).
 // ---------------------------------------------------------------------------------------
-template <typename T> struct mid_planes {
-    T *r11, *r12, *r22, *tth, *secth;
-    int32_t *s, *bits;
-};
+constexpr int64_t SPLIT_MIN = 1 << 16;                    // smaller batches: the fused kernel
+
 // Which quotients use the FP64 divider (csdiv): the three of eq. (QR15) in phases 1-2, none
 // in phase 3.  Phases 1-2 are integer-heavy (the hypots, eq. (EXT)) and phase 3 FP64-heavy,
 // so the FP64 divider moves to the first half: on 2^26 wide-range matrices 19.1 ms against
 // 24.1 ms with the fused kernel's placement (the cos/sin quotients of Alg. 1 and 2 on the
 // divider), 20.0 with both, 20.3 with neither.
-constexpr bool SPLIT_FDIV_A = true, SPLIT_FDIV_B = false;
-// bits: t | t' << 4 | phase-1-2 flags << 8 | c15 << 16 | pu << 17 | pv << 18 | na << 19 |
-// nb << 20 | n12 << 21 | n22 << 22 | MID_B (phase 3 still to run)
-constexpr int32_t MID_B = 1 << 23;
+#ifndef K2_SPLIT_FDIV_T
+#define K2_SPLIT_FDIV_T 1
+#endif
+#ifndef K2_SPLIT_FDIV_R
+#define K2_SPLIT_FDIV_R 1
+#endif
+constexpr bool SPLIT_FDIV_A = K2_SPLIT_FDIV_R, SPLIT_FDIV_AT = K2_SPLIT_FDIV_T, SPLIT_FDIV_B = false;
 
-template <typename T, bool NCR>
-__global__ void __launch_bounds__(256, 8) svd2a_kernel(const svd_args<T> a, const mid_planes<T> mp)
+// The packed word in the sigma1 plane: bit 63 set (phase 3 pending); bits 0-3 t, 4-7 t',
+// 8-15 phase-1-2 flags, 16 c15, 17 pu, 18 pv, 19 na, 20 nb, 21 n12, 22 n22; bits 32-47 the
+// prescaling exponent s + 32768 (|s| < 2200).
+__device__ __forceinline__ uint64_t mid_pack(const svd2_mid<double> &m)
+{
+    const uint32_t lo = (uint32_t)(m.t | (m.tp << 4) | (m.flags << 8) | (m.c15 << 16) | (m.pu << 17) | (m.pv << 18) |
+                                   (m.na << 19) | (m.nb << 20) | (m.n12 << 21) | (m.n22 << 22));
+    return D_SIGN | ((uint64_t)(uint32_t)(m.s + 32768) << 32) | lo;
+}
+__device__ __forceinline__ void mid_unpack(uint64_t w, svd2_mid<double> &m)
+{
+    const uint32_t b = (uint32_t)w;
+    m.t = b & 15; m.tp = (b >> 4) & 15; m.flags = (b >> 8) & 255;
+    m.c15 = (b >> 16) & 1; m.pu = (b >> 17) & 1; m.pv = (b >> 18) & 1; m.na = (b >> 19) & 1;
+    m.nb = (b >> 20) & 1; m.n12 = (b >> 21) & 1; m.n22 = (b >> 22) & 1;
+    m.s = (int)((uint32_t)(w >> 32) & 0xFFFF) - 32768;
+}
+
+// Phases 1-2.  Matrices finished here (the simple classes, the fallback, non-finite inputs)
+// get their results; the others get the parked state.
+template <bool NCR>
+__global__ void __launch_bounds__(256, 8) svd2a_kernel(const svd_args<double> a)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const T g11 = __ldcs(a.g0 + i), g21 = __ldcs(a.g1 + i), g12 = __ldcs(a.g2 + i), g22 = __ldcs(a.g3 + i);
-        svd2_out<T> o;
-        svd2_mid<T> m;
+        const double g11 = __ldcs(a.g0 + i), g21 = __ldcs(a.g1 + i), g12 = __ldcs(a.g2 + i), g22 = __ldcs(a.g3 + i);
+        svd2_out<double> o;
+        svd2_mid<double> m;
         if (is_fin(g11) && is_fin(g21) && is_fin(g12) && is_fin(g22)) {
-            if (svd2_a<T, NCR, SPLIT_FDIV_A>(g11, g21, g12, g22, o, m)) {
-                mp.r11[i] = m.r11; mp.r12[i] = m.r12; mp.r22[i] = m.r22;
-                if (m.c15) { mp.tth[i] = m.tth; mp.secth[i] = m.secth; }
-                mp.s[i] = m.s;
-                mp.bits[i] = m.t | (m.tp << 4) | (m.flags << 8) | (m.c15 << 16) | (m.pu << 17) | (m.pv << 18) |
-                             (m.na << 19) | (m.nb << 20) | (m.n12 << 21) | (m.n22 << 22) | MID_B;
+            if (svd2_a<double, NCR, SPLIT_FDIV_A, SPLIT_FDIV_AT>(g11, g21, g12, g22, o, m)) {
+                a.u0[i] = m.r11; a.u1[i] = m.r12; a.u2[i] = m.r22;
+                if (m.c15) { a.u3[i] = m.tth; a.v0[i] = m.secth; }
+                a.s1[i] = dfrom(mid_pack(m));
                 continue;
             }
         } else {
             nan_out(o);
         }
-        mp.bits[i] = 0;
         store_out(a, i, o);
     }
 }
 
-template <typename T, bool NCR>
-__global__ void __launch_bounds__(256, 8) svd2b_kernel(const svd_args<T> a, const mid_planes<T> mp)
+// Phase 3 for the matrices whose sigma1 plane holds a packed word (sign bit set).
+template <bool NCR>
+__global__ void __launch_bounds__(256, 8) svd2b_kernel(const svd_args<double> a)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const int32_t b = __ldcs(mp.bits + i);
-        if (!(b & MID_B)) continue;
-        svd2_mid<T> m;
-        m.t = b & 15; m.tp = (b >> 4) & 15; m.flags = (b >> 8) & 255;
-        m.c15 = (b >> 16) & 1; m.pu = (b >> 17) & 1; m.pv = (b >> 18) & 1; m.na = (b >> 19) & 1;
-        m.nb = (b >> 20) & 1; m.n12 = (b >> 21) & 1; m.n22 = (b >> 22) & 1;
-        m.s = __ldcs(mp.s + i);
-        m.r11 = __ldcs(mp.r11 + i); m.r12 = __ldcs(mp.r12 + i); m.r22 = __ldcs(mp.r22 + i);
-        if (m.c15) { m.tth = __ldcs(mp.tth + i); m.secth = __ldcs(mp.secth + i); }
-        else { m.tth = T(0); m.secth = T(0); }
-        svd2_out<T> o;
-        svd2_b<T, SPLIT_FDIV_B, NCR>(m, o);
+        const uint64_t w = dbits(a.s1[i]);
+        if (!(w & D_SIGN)) continue;
+        svd2_mid<double> m;
+        mid_unpack(w, m);
+        m.r11 = a.u0[i]; m.r12 = a.u1[i]; m.r22 = a.u2[i];
+        if (m.c15) { m.tth = a.u3[i]; m.secth = a.v0[i]; }
+        else { m.tth = 0.0; m.secth = 0.0; }
+        svd2_out<double> o;
+        svd2_b<double, SPLIT_FDIV_B, NCR>(m, o);
         store_out(a, i, o);
     }
 }
 
-// A private stream-ordered memory pool per device for the split form's scratch: allocations
-// are ordered on the caller's stream (safe for concurrent calls on several streams) and the
-// pool keeps up to SPLIT_KEEP bytes between calls.
-constexpr int64_t SPLIT_CHUNK = 1 << 24;                  // matrices per pair of launches
-constexpr int64_t SPLIT_MIN = 1 << 16;                    // smaller batches: the fused kernel
-constexpr uint64_t SPLIT_KEEP = 1ull << 30;
-
-static cudaMemPool_t split_pool(int dev)
-{
-    static std::mutex mu;
-    static cudaMemPool_t pools[64] = {};
-    if (dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> g(mu);
-    if (!pools[dev]) {
-        cudaMemPoolProps pp = {};
-        pp.allocType = cudaMemAllocationTypePinned;
-        pp.location.type = cudaMemLocationTypeDevice;
-        pp.location.id = dev;
-        cudaMemPool_t p;
-        if (cudaMemPoolCreate(&p, &pp) != cudaSuccess) { cudaGetLastError(); return nullptr; }
-        uint64_t keep = SPLIT_KEEP;
-        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
-        pools[dev] = p;
-    }
-    return pools[dev];
-}
-
-template <typename T> static svd_args<T> shifted(const svd_args<T> &a, int64_t off, int64_t len)
-{
-    svd_args<T> b = a;
-    b.g0 += off; b.g1 += off; b.g2 += off; b.g3 += off;
-    b.u0 += off; b.u1 += off; b.u2 += off; b.u3 += off;
-    b.v0 += off; b.v1 += off; b.v2 += off; b.v3 += off;
-    b.s1 += off; b.s2 += off;
-    if (b.se1) { b.se1 += off; b.se2 += off; }
-    if (b.sf1) { b.sf1 += off; b.sf2 += off; }
-    if (b.info) b.info += off;
-    b.n = len;
-    return b;
-}
-
-// The split form (falls back to the fused kernel when no scratch can be had).
-template <typename T, bool NCR>
-static int launch_split(const svd_args<T> &a, cudaStream_t st)
+// The split form: two launches over the whole batch, no allocation.
+template <bool NCR>
+static int launch_split(const svd_args<double> &a, cudaStream_t st)
 {
     static thread_local int cdev = -1, cblocks_a = 0, cblocks_b = 0;
     int dev;
     if (cudaGetDevice(&dev) != cudaSuccess) return K2SVD_ECUDA;
     if (dev != cdev) {
         int na = 0, nb = 0;
-        if (grid_for(svd2a_kernel<T, NCR>, 256, 0, &na) != 0) return K2SVD_ECUDA;
-        if (grid_for(svd2b_kernel<T, NCR>, 256, 0, &nb) != 0) return K2SVD_ECUDA;
+        if (grid_for(svd2a_kernel<NCR>, 256, 0, &na) != 0) return K2SVD_ECUDA;
+        if (grid_for(svd2b_kernel<NCR>, 256, 0, &nb) != 0) return K2SVD_ECUDA;
         cdev = dev; cblocks_a = na; cblocks_b = nb;
     }
-    const int64_t chunk = a.n < SPLIT_CHUNK ? a.n : SPLIT_CHUNK;
-    const size_t bytes = (size_t)chunk * (5 * sizeof(T) + 2 * sizeof(int32_t));
-    cudaMemPool_t pool = split_pool(dev);
-    void *ws = nullptr;
-    if (!pool || cudaMallocFromPoolAsync(&ws, bytes, pool, st) != cudaSuccess) {
-        cudaGetLastError();                                   // no scratch: the fused kernel
-        return launch<T, false, NCR>(a, st);
-    }
-    mid_planes<T> mp;
-    T *tp = (T *)ws;
-    mp.r11 = tp; mp.r12 = tp + chunk; mp.r22 = tp + 2 * chunk; mp.tth = tp + 3 * chunk; mp.secth = tp + 4 * chunk;
-    mp.s = (int32_t *)(tp + 5 * chunk); mp.bits = mp.s + chunk;
-    for (int64_t off = 0; off < a.n; off += chunk) {
-        const int64_t len = (a.n - off) < chunk ? (a.n - off) : chunk;
-        const svd_args<T> b = shifted(a, off, len);
-        const int64_t need = (len + 255) / 256;
-        svd2a_kernel<T, NCR><<<(int)(need < cblocks_a ? need : cblocks_a), 256, 0, st>>>(b, mp);
-        svd2b_kernel<T, NCR><<<(int)(need < cblocks_b ? need : cblocks_b), 256, 0, st>>>(b, mp);
-    }
-    const cudaError_t e = cudaPeekAtLastError();
-    cudaFreeAsync(ws, st);
-    return e == cudaSuccess ? 0 : K2SVD_ECUDA;
+    const int64_t need = (a.n + 255) / 256;
+    svd2a_kernel<NCR><<<(int)(need < cblocks_a ? need : cblocks_a), 256, 0, st>>>(a);
+    svd2b_kernel<NCR><<<(int)(need < cblocks_b ? need : cblocks_b), 256, 0, st>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : K2SVD_ECUDA;
 }
 
 // General matrices: the split form for double batches of SPLIT_MIN or more, the fused
-// kernel for smaller ones (one launch, no scratch), for float and for the variant with the
-// hypot that is not correctly rounded.
+// kernel for smaller ones (one launch), for float and for the variant with the hypot that is
+// not correctly rounded.
 template <typename T, bool NCR>
 static int launch_general(const svd_args<T> &a, cudaStream_t st)
 {
     if constexpr (sizeof(T) == 8 && !NCR) {
-        if (a.n >= SPLIT_MIN) return launch_split<T, NCR>(a, st);
+        if (a.n >= SPLIT_MIN) return launch_split<NCR>(a, st);
     }
     return launch<T, false, NCR>(a, st);
 }

@@ -14,6 +14,7 @@ import torch
 from . import build as _build
 
 _lib = None
+_probe = None
 
 INFO_FLAGS = {"ext": 1 << 8, "fallback": 1 << 9, "swap": 1 << 10, "t2f2": 1 << 11,
               "t2f3": 1 << 12, "t2inf": 1 << 13, "tpinf": 1 << 14, "psig": 1 << 15}
@@ -43,6 +44,18 @@ def lib():
         _bind_extra(L)
         _lib = L
     return _lib
+
+
+def probe_lib():
+    """The loaded measurement library libk2probe (include/k2probe.h): pipe-rate probes and
+    elementwise checks of the division and hypot primitives; not part of the method."""
+    global _probe
+    if _probe is None:
+        path = _build.PROBE_LIB
+        if not os.path.exists(path):
+            raise K2SVDError("libk2probe is not built (%s missing); run __graft_entry__.build()" % path)
+        _probe = C.CDLL(path)
+    return _probe
 
 
 def _bind_extra(L):

@@ -8,9 +8,9 @@ import re
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
+def _declared(header=None):
     names = set()
-    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+    for h in glob.glob(os.path.join(ROOT, "include", header or "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         names.update(re.findall(r"^\s*int\s+(k2\w+)\s*\(", src, flags=re.M))
@@ -25,12 +25,18 @@ def test_headers_declare_the_abi():
 
 
 def test_library_exports_every_declared_symbol():
+    """libk2svd exports every function of k2svd.h and no probe; libk2probe every function of
+    k2probe.h."""
     from paper_2407_13116_gb300 import build
     path = build.build()
     lib = ctypes.CDLL(path)
-    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    missing = [n for n in sorted(_declared("k2svd.h")) if not hasattr(lib, n)]
     assert not missing, missing
     assert lib.k2svd_version() == 100
+    assert not any(hasattr(lib, n) for n in _declared("k2probe.h"))
+    probe = ctypes.CDLL(build.PROBE_LIB)
+    missing = [n for n in sorted(_declared("k2probe.h")) if not hasattr(probe, n)]
+    assert not missing, missing
 
 
 def test_headers_compile_as_c99_and_cpp(tmp_path):

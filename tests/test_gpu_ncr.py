@@ -24,7 +24,7 @@ def k2():
 
 
 def _lib():
-    L = k2().lib()
+    L = k2().probe_lib()
     for f in ("k2probe_hypot_ncr", "k2probe_hypotf_ncr"):
         getattr(L, f).argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         getattr(L, f).restype = C.c_int

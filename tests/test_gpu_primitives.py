@@ -18,7 +18,7 @@ DEV = "cuda:0"
 
 def _lib():
     from paper_2407_13116_gb300 import k2svd
-    L = k2svd.lib()
+    L = k2svd.probe_lib()
     for f in ("k2probe_div", "k2probe_hypot", "k2probe_hypotf"):
         getattr(L, f).argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         getattr(L, f).restype = C.c_int

@@ -223,3 +223,40 @@ def test_full_size_sampled_parity(prec):
         _assert_same(got, ref, "full-size %s %s" % (tag, prec))
     del G, T3, outg, outt
     torch.cuda.empty_cache()
+
+
+def test_split_path_many_chunks_parity():
+    """The FP64 general path on more than 2^24 matrices: many chunks of the two-launch split
+    form with its state parked in the output planes, a ragged last chunk, non-finite inputs
+    and all optional outputs; every matrix checked against the oracle bit for bit, and
+    nothing written past the batch."""
+    n = (1 << 24) + 4097
+    G = I.general(n, 4300, "d", "narrow")
+    rng = np.random.default_rng(11)
+    bad = rng.integers(0, n, 64)
+    G[rng.integers(0, 4, 64), bad] = np.where(np.arange(64) % 2 == 0, np.nan, -np.inf)
+    ld = n + 3
+    Gt = torch.zeros((4, ld), dtype=torch.float64, device=DEV)
+    Gt[:, :n] = torch.from_numpy(G).to(DEV)
+    U = torch.full((4, ld), 7.0, dtype=torch.float64, device=DEV)
+    V = torch.full((4, ld), 7.0, dtype=torch.float64, device=DEV)
+    S = torch.full((2, ld), 7.0, dtype=torch.float64, device=DEV)
+    Se = torch.full((2, ld), 7, dtype=torch.int32, device=DEV)
+    Sf = torch.full((2, ld), 7.0, dtype=torch.float64, device=DEV)
+    info = torch.full((ld,), 7, dtype=torch.int32, device=DEV)
+    import ctypes as C
+    p = lambda t: C.c_void_p(t.data_ptr())
+    rc = k2().lib().k2svd_dgesvd2(n, p(Gt), ld, p(U), ld, p(V), ld, p(S), ld, p(Se), p(Sf), p(info),
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    got = {"U": U[:, :n].cpu().numpy(), "V": V[:, :n].cpu().numpy(), "S": S[:, :n].cpu().numpy(),
+           "Se": Se[:, :n].cpu().numpy(), "Sf": Sf[:, :n].cpu().numpy(), "info": info[:n].cpu().numpy()}
+    ref = oracle.gesvd2(G, "d", nthreads=16)
+    assert (ref["info"] == -1).sum() >= 32
+    _assert_same(got, ref, "split chunks")
+    for t in (U, V, S, Sf):
+        assert (t[:, n:] == 7.0).all()
+    assert (Se[:, n:] == 7).all() and (info[n:] == 7).all()
+    del Gt, U, V, S, Se, Sf, info
+    torch.cuda.empty_cache()
