@@ -27,12 +27,12 @@ sys.path.insert(0, ROOT)
 SEED = 0x240713116
 N_HALF_D = 1 << 27
 N_HALF_S = 1 << 28
-E2E_HALF = 1 << 25
+E2E_HALF = 1 << 27
 N_DIFF = 1 << 24
 N_KOG = 8192
 N_COMPLEX = 1 << 26
 N_RECT = 2048
-E2E_CHUNK = 1 << 21
+E2E_CHUNK = 1 << 22
 METRIC = "FP64 2×2 SVDs/s & % of roofline; fwd+bwd/s; batched Kogbetliantz speedup"
 BYTES_GE = {"d": 112, "s": 56}          # in 4 T + out (4 U + 4 V + 2 S) T
 BYTES_TR = {"d": 104, "s": 52}          # in 3 T + out 10 T
@@ -53,7 +53,11 @@ def parse():
     p.add_argument("--no-complex", action="store_true")
     p.add_argument("--no-rect", action="store_true")
     p.add_argument("--no-ncr", action="store_true")
-    p.add_argument("--profile-case", choices=["d", "s", "dn", "sn", "kog", "z"], default=None,
+    p.add_argument("--no-kog-grad", action="store_true")
+    p.add_argument("--no-narrow", action="store_true")
+    p.add_argument("--summarize-ncu", default=None, help="print per-pipe counts per unit from an ncu --csv log")
+    p.add_argument("--units", default="", help="with --summarize-ncu: substring=units per launch, ...")
+    p.add_argument("--profile-case", choices=["d", "s", "dn", "sn", "kog", "z", "misc"], default=None,
                    help="run a small case of the 2x2 kernels (d, s; dn, sn: the variant with the hypot "
                         "that is not correctly rounded), of the complex kernel (z) or of the persistent "
                         "Kogbetliantz kernel (kog), for ncu captures, and exit")
@@ -160,22 +164,142 @@ class Clocks:
 # ----------------------------------------------------------------------------------------
 # roofline bookkeeping
 # ----------------------------------------------------------------------------------------
-# DRAM traffic of the gesvd2 double kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of `python bench.py --profile-case d` (2^22 matrices), scaled by
-# the matrix count to a full 2^27-matrix launch.  Valid only for the kernel sources with
-# this hash; any change to them reports null until a new capture is taken.
-TRAFFIC_SRC_HASH = "6187dd399f2925fc"
-TRAFFIC_BYTES_PER_MATRIX = (136.719616e6 + 291.307776e6 + 201.474304e6 + 344.086272e6) / (1 << 22)
-KERNEL_SOURCES = ("k2_fp.cuh", "k2_svd2.cuh", "k2_svd2_kernel.cuh", "k2_gesvd2.cu")
+# ----------------------------------------------------------------------------------------
+# Per-pipe instruction ceilings.  A kernel cannot finish faster than its busiest pipe can
+# issue the warp instructions it executes, so for each pipe P the time
+#     t_P = (warp instructions on P per unit) x units / (peak rate of P per SM per clock x SMs x clock)
+# is a lower bound on the kernel's duration, and the kernel's ceiling is the largest t_P.
+# The counts per unit come from one ncu capture of each kernel on a small case of the same
+# workload (bench.py --profile-case ..., summarised by --summarize-ncu into the tables of
+# profiles/pipe_ceilings.md); the clock is the median SM clock sampled during the timed
+# region.  A count table is valid only for the kernel sources whose hash it was taken at;
+# after any change to them the ceiling is reported as null until a new capture is taken.
+# ----------------------------------------------------------------------------------------
+PIPE_METRIC = {"issue": "sm__inst_executed", "fp64": "sm__inst_executed_pipe_fp64",
+               "alu": "sm__inst_executed_pipe_alu", "fmaheavy": "sm__inst_executed_pipe_fmaheavy",
+               "fmalite": "sm__inst_executed_pipe_fmalite", "fma": "sm__inst_executed_pipe_fma",
+               "lsu": "sm__inst_executed_pipe_lsu", "xu": "sm__inst_executed_pipe_xu",
+               "cbu": "sm__inst_executed_pipe_cbu", "adu": "sm__inst_executed_pipe_adu",
+               "uniform": "sm__inst_executed_pipe_uniform"}
+# warp instructions per clock per SM (ncu `<metric>.sum.peak_sustained` on a GB300 / 152 SMs)
+PIPE_PEAK = {"issue": 4.0, "fp64": 1.0 / 16, "alu": 2.0, "fmaheavy": 2.0, "fmalite": 2.0, "fma": 4.0,
+             "lsu": 1.0, "xu": 1.0, "cbu": 4.0, "adu": 0.5, "uniform": 2.0}
+SRC_2X2 = ("k2_fp.cuh", "k2_svd2.cuh", "k2_svd2_kernel.cuh", "k2_gesvd2.cu")
+SRC_GROUPS = {"2x2": SRC_2X2, "complex": SRC_2X2 + ("k2_complex.cu",), "bwd": ("k2_bwd.cu",),
+              "kog": SRC_2X2 + ("k2_kog.cu", "k2_kog_dev.cuh")}
+# kernel -> (source group, unit, {pipe: warp instructions per unit}, DRAM bytes per unit)
+PIPE_COUNTS_HASH = {}
+PIPE_COUNTS = {}
 
 
-def kernel_hash():
+def src_hash(group):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in SRC_GROUPS[group]:
         with open(os.path.join(ROOT, "paper_2407_13116_gb300", "csrc", f), "rb") as fh:
             h.update(hashlib.sha256(fh.read()).hexdigest().encode() + b"  " + f.encode() + b"\n")
     return h.hexdigest()[:16]
+
+
+def sm_count():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def ceiling(kernels, units, clock_mhz):
+    """Lower bound (seconds) on the summed duration of `kernels` processing `units` units
+    each, from their per-pipe instruction counts; None when a count table is missing or was
+    taken at other kernel sources.  Returns (seconds, {kernel: binding pipe}, DRAM bytes)."""
+    sms, f = sm_count(), clock_mhz * 1e6
+    total, pipes, dram = 0.0, {}, 0.0
+    for k in kernels:
+        if k not in PIPE_COUNTS:
+            return None
+        group, _, per, dbytes = PIPE_COUNTS[k]
+        if PIPE_COUNTS_HASH.get(group) != src_hash(group):
+            return None
+        t = {p: c * units / (PIPE_PEAK[p] * sms * f) for p, c in per.items()}
+        b = max(t, key=t.get)
+        total += t[b]
+        pipes[k] = b
+        dram += dbytes * units
+    return total, pipes, dram
+
+
+def roofline_entry(kernels, units, unit_name, measured_s, clock_mhz, algorithmic_bytes, fp64_model=None):
+    """The bench line's roofline object for kernels timed together (CUDA events): achieved
+    units/s against the per-pipe instruction ceiling at the sampled clock."""
+    c = ceiling(kernels, units, clock_mhz)
+    hbm, hbm_src = hbm_peak_gbs()
+    out = {"bound": "alu", "unit": unit_name + "/s", "achieved": units / measured_s, "kernels": list(kernels),
+           "kernel_ms": measured_s * 1e3, "algorithmic_bytes": algorithmic_bytes,
+           "hbm_frac": (algorithmic_bytes / measured_s / (hbm * 1e9)) if algorithmic_bytes else None,
+           "clock_mhz": clock_mhz}
+    if c is None:
+        out.update({"peak": None, "frac": None, "traffic": None,
+                    "note": "no per-pipe count table for the current kernel sources"})
+    else:
+        t, pipes, dram = c
+        out.update({"peak": units / t, "frac": t / measured_s, "traffic": dram, "binding_pipe": pipes,
+                    "ceiling_ms": t * 1e3,
+                    "peak_source": "per-pipe warp-instruction counts (ncu, profiles/pipe_ceilings.md) at the pipes' "
+                                   "issue rates (ncu peak_sustained) x %d SMs x the median SM clock %.0f MHz sampled "
+                                   "during the timed region" % (sm_count(), clock_mhz)})
+    if fp64_model is not None:
+        out["fp64_model_frac"] = fp64_model
+    return out
+
+
+def summarize_ncu(path, units_spec):
+    """Per-kernel per-pipe warp instructions per unit from an ncu --csv metrics log (the
+    metrics of profiles/pipe_ceilings.md); units_spec: 'substring=units,...' (units per
+    launch of the kernels whose name contains substring, or 'total:' + units for all
+    launches of the kernel together).  Prints a markdown table and the count literals."""
+    import collections
+    import csv
+    rows = [r for r in csv.reader(open(path)) if len(r) > 14 and r[0] != "ID"]
+    launches = collections.OrderedDict()
+    for r in rows:
+        try:
+            v = float(r[14].replace(",", ""))
+        except ValueError:
+            continue
+        launches.setdefault(r[0], {"name": r[4]})[r[12]] = v
+    spec = [kv.split("=") for kv in units_spec.split(",")] if units_spec else []
+    agg = collections.OrderedDict()
+    for d in launches.values():
+        a = agg.setdefault(d["name"], collections.defaultdict(float))
+        a["launches"] += 1
+        a["cycles"] += d.get("sm__cycles_elapsed.max", 0.0)
+        a["ms"] += d.get("gpu__time_duration.sum", 0.0) / 1e6
+        a["dram"] += d.get("dram__bytes_read.sum", 0.0) + d.get("dram__bytes_write.sum", 0.0)
+        for p, m in PIPE_METRIC.items():
+            a[p] += d.get(m + ".sum", 0.0)
+        for k in ("smsp__thread_inst_executed_per_inst_executed.ratio", "launch__registers_per_thread",
+                  "sm__cycles_elapsed.avg.per_second"):
+            a[k] = d.get(k, 0.0)
+    print("| kernel | launches | units | ms | clock MHz | lanes | " + " | ".join(PIPE_METRIC) +
+          " | busiest pipe, fraction of elapsed | DRAM B/unit |")
+    print("|" + "---|" * (len(PIPE_METRIC) + 8))
+    lits = {}
+    for nm, a in agg.items():
+        units = None
+        for sub, u in spec:
+            if sub in nm:
+                units = float(u[6:]) if u.startswith("total:") else float(u) * a["launches"]
+        if not units:
+            continue
+        per = {p: a[p] / units for p in PIPE_METRIC}
+        frac = {p: a[p] / (PIPE_PEAK[p] * 152) / a["cycles"] for p in PIPE_METRIC}
+        b = max(frac, key=frac.get)
+        print("| %s | %d | %.6g | %.3f | %.0f | %.1f | %s | %s %.3f | %.1f |" % (
+            nm, a["launches"], units, a["ms"], a["sm__cycles_elapsed.avg.per_second"] / 1e6,
+            a["smsp__thread_inst_executed_per_inst_executed.ratio"],
+            " | ".join("%.4g" % per[p] for p in PIPE_METRIC), b, frac[b], a["dram"] / units))
+        lits[nm] = {p: float("%.5g" % per[p]) for p in PIPE_METRIC}, float("%.5g" % (a["dram"] / units))
+    print()
+    for nm, (per, d) in lits.items():
+        print(repr(nm), per, d)
 
 
 def fp64_peak(clock_mhz):
@@ -382,11 +506,17 @@ def fwd_bwd_leg(steps, warmup, dev, D, rates, clk_mhz):
             "workload": "2^24 FP64 R(theta) diag(s1,s2) R(phi)^T, 10% near-equal singular values, upstream N(0,1)"}
 
 
-def kog_leg(steps, warmup, dev, D):
+KOG_BUCKETS = ((8, 32), (33, 64), (65, 96), (97, 128))
+
+
+def kog_leg(steps, warmup, dev, D, rates):
     """Batched Kogbetliantz: 8192 FP64 matrices of order uniform in {8..128} (Q1 diag(sigma)
     Q2^T, sigma log-uniform in [1e-12, 1]) to off-norm < n eps ||G||_F.  The persistent form
-    (one graph launch of per-bucket persistent kernels) is timed over `steps` runs; the
-    per-step form (three launches per step, a host read-back per sweep) once."""
+    (one graph launch of per-bucket persistent kernels) is timed over `steps` runs with the
+    SM clock sampled; the per-step form (three launches per step, a host read-back per sweep)
+    after one warm-up run, median of three.  Beside them: each order range alone, the
+    rotation floor (the 8 n^3 FP64 operations per sweep of the row, column, U and V
+    rotations at the FP64 pipe's rate) and the per-pipe instruction ceiling."""
     import numpy as np
     import torch
     from paper_2407_13116_gb300 import inputs as I
@@ -404,23 +534,61 @@ def kog_leg(steps, warmup, dev, D):
         run(k2svd.KOG_GRAPH, ws)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(D.local)
+    clk.start()
     D.barrier()
     e0.record()
     for _ in range(steps):
         run(k2svd.KOG_GRAPH, ws)
     e1.record()
     torch.cuda.synchronize()
+    clocks = clk.stop()
     pers_ms = D.max(e0.elapsed_time(e1) / steps)
+    clk_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     sweeps = sw.cpu().numpy().astype(np.int64)
     conv = int((info.cpu().numpy() == 0).sum())
     Sp = S.clone()
     wsp = k2svd.kogbet_workspace(orders, torch.float64, k2svd.KOG_PLAIN, dev)
+    run(k2svd.KOG_PLAIN, wsp)                   # warm-up of the per-step form
     torch.cuda.synchronize()
-    t = time.perf_counter()
-    run(k2svd.KOG_PLAIN, wsp)
-    torch.cuda.synchronize()
-    plain_ms = D.max((time.perf_counter() - t) * 1e3)
+    plain = []
+    for _ in range(3):
+        t = time.perf_counter()
+        run(k2svd.KOG_PLAIN, wsp)
+        torch.cuda.synchronize()
+        plain.append((time.perf_counter() - t) * 1e3)
+    plain_ms = D.max(statistics.median(plain))
     same = bool(torch.equal(Sp, S))
+    del wsp
+    nn = orders.astype(np.int64)
+    rot = sweeps * 8 * nn ** 3                  # FP64 operations of the rotations, per matrix
+    sms = sm_count()
+    nominal = sms * 2.0 * clk_mhz * 1e6         # 2 DFMA per clock per SM
+    floor_ms = float(rot.sum()) / nominal * 1e3
+    floor_probe_ms = float(rot.sum()) / rates["dfma"] * 1e3
+    # each order range alone (same matrices, same form)
+    buckets = {}
+    for lo, hi in KOG_BUCKETS:
+        sel = np.flatnonzero((orders >= lo) & (orders <= hi))
+        if len(sel) == 0:
+            continue
+        ob = orders[sel]
+        Ab = torch.from_numpy(np.concatenate([flat[offs[i]:offs[i] + orders[i] ** 2] for i in sel])).to(dev)
+        nb_, ob_offs, ob_soffs, tb, sb = k2svd.kog_layout(ob)
+        Ub = torch.empty(tb, dtype=torch.float64, device=dev); Vb = torch.empty_like(Ub)
+        Sb = torch.empty(sb, dtype=torch.float64, device=dev)
+        wsb = k2svd.kogbet_workspace(ob, torch.float64, k2svd.KOG_GRAPH, dev)
+        runb = lambda: k2svd.kogbet(Ab, ob, flags=k2svd.KOG_GRAPH, workspace=wsb, U=Ub, V=Vb, S=Sb)
+        runb()
+        torch.cuda.synchronize()
+        tb_ms = []
+        for _ in range(3):
+            e0.record(); runb(); e1.record(); torch.cuda.synchronize()
+            tb_ms.append(e0.elapsed_time(e1))
+        bf = float(rot[sel].sum()) / nominal * 1e3
+        buckets["%d..%d" % (lo, hi)] = {"matrices": int(len(sel)), "ms": statistics.median(tb_ms),
+                                        "rotation_floor_ms": bf, "over_floor": statistics.median(tb_ms) / bf}
+        del Ab, Ub, Vb, Sb, wsb
     # the dynamic pivot ordering (persistent graph form), same matrices and stopping rule
     wsd = k2svd.kogbet_workspace(orders, torch.float64, k2svd.KOG_GRAPH | k2svd.KOG_DYNAMIC, dev)
     for _ in range(warmup + 1):
@@ -435,24 +603,111 @@ def kog_leg(steps, warmup, dev, D):
     dyn_sweeps = sw.cpu().numpy().astype(np.int64)
     dyn_conv = int((info.cpu().numpy() == 0).sum())
     del wsd
-    nn = orders.astype(np.int64)
-    # method's FP64 work: per sweep n(n-1)/2 pivots, each a 2x2 SVD (~239 FP64 slots, the
-    # general double count) and 16 FP64 operations per index (row, column, U and V rotations)
+    # BASELINE's FP64 model: per sweep n(n-1)/2 pivots at 239 FP64 slots and 16 n FP64
+    # operations per pivot for the rotations
     ops = float((sweeps * (nn * (nn - 1) // 2) * (16 * nn + 239)).sum())
-    peak = fp64_peak(2070.0)
-    del A, U, V, S, ws, wsp
+    roof = roofline_entry(["kog_persistent"], float(rot.sum()), "rotation FP64 op", pers_ms / 1e3, clk_mhz, None,
+                          fp64_model=ops / (pers_ms / 1e3) / nominal)
+    roof["unit_note"] = ("units are the rotations' FP64 operations (8 n^3 per sweep); the ceiling scales the "
+                         "instructions counted per such operation on a 608-matrix sample of the same order mix")
+    del A, U, V, S, ws
     torch.cuda.empty_cache()
     return {"speedup_vs_per_step": plain_ms / pers_ms, "persistent_ms": pers_ms, "per_step_ms": plain_ms,
-            "matrices_per_gpu": N_KOG, "converged": conv, "mean_sweeps": float(sweeps.mean()),
-            "max_sweeps": int(sweeps.max()), "forms_bitwise_equal": same,
-            "roofline": {"bound": "alu", "achieved": ops / (pers_ms / 1e3) / 1e9, "peak": peak / 1e9,
-                         "unit": "G FP64-pipe op/s", "frac": ops / (pers_ms / 1e3) / peak,
-                         "ops": ops},
+            "per_step_runs_ms": plain, "matrices_per_gpu": N_KOG, "converged": conv,
+            "mean_sweeps": float(sweeps.mean()), "max_sweeps": int(sweeps.max()), "forms_bitwise_equal": same,
+            "rotation_floor_ms": floor_ms, "rotation_floor_probe_ms": floor_probe_ms,
+            "over_rotation_floor": pers_ms / floor_ms,
+            "max_speedup_at_floor": plain_ms / floor_ms,
+            "buckets": buckets, "clocks": clocks, "roofline": roof,
             "dynamic_ordering": {"persistent_ms": dyn_ms, "speedup_vs_per_step": plain_ms / dyn_ms,
                                  "vs_modulus_persistent": pers_ms / dyn_ms, "mean_sweeps": float(dyn_sweeps.mean()),
                                  "max_sweeps": int(dyn_sweeps.max()), "converged": dyn_conv},
             "workload": "8192 FP64 Q1 diag(sigma) Q2^T, n uniform in {8..128}, sigma log-uniform [1e-12,1], "
                         "modulus strategy (and the dynamic ordering beside it), off < n eps ||G||_F"}
+
+
+def kog_grad_leg(steps, warmup, dev, D):
+    """Batched Kogbetliantz with gradients: 2048 FP64 matrices of order uniform in {32..256}
+    and 4096 FP32 matrices of order uniform in {8..128}, built as the batched workload.  A step
+    is, for each batch, the forward (persistent graph form) and the gradient of sum(dS * S)
+    with respect to A (dA = U diag(dS) V^T) through the autograd Function, dS ~ N(0,1)."""
+    import numpy as np
+    import torch
+    from paper_2407_13116_gb300 import inputs as I
+    from paper_2407_13116_gb300 import k2svd
+    from paper_2407_13116_gb300.autograd import kogbet_sigma
+    seed = shard_seed(SEED + 5, D.rank)
+    parts = []
+    for count, lo, hi, dt, sd in ((2048, 32, 256, np.float64, seed), (4096, 8, 128, np.float32, seed + 1)):
+        o = I.kog_orders(count, lo, hi, sd)
+        f, _ = I.kog_batch(o, sd, dtype=dt)
+        A = torch.from_numpy(f).to(dev).requires_grad_(True)
+        stot = int(k2svd.kog_layout(o)[4])
+        gen = torch.Generator(device=dev).manual_seed(sd)
+        dS = torch.randn(stot, dtype=A.dtype, device=dev, generator=gen)
+        parts.append((o, A, dS))
+
+    def one(o, A, dS):
+        U, S, V, sw, info = kogbet_sigma(A, o, flags=k2svd.KOG_GRAPH)
+        (dA,) = torch.autograd.grad(S, A, dS)
+        return sw, info
+
+    for _ in range(warmup + 1):                 # the first call tunes the block sizes
+        for p_ in parts:
+            one(*p_)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    D.barrier()
+    for k in range(steps):
+        ev[k][0].record()
+        sw64, info64 = one(*parts[0])
+        ev[k][1].record()
+        sw32, info32 = one(*parts[1])
+        ev[k][2].record()
+    torch.cuda.synchronize()
+    ms64 = statistics.median(e[0].elapsed_time(e[1]) for e in ev)
+    ms32 = statistics.median(e[1].elapsed_time(e[2]) for e in ev)
+    ms = D.max(ms64 + ms32)
+    out = {"value": D.world * (2048 + 4096) / (ms / 1e3), "unit": "matrices/s (forward + sigma gradient)",
+           "ms_per_step": ms, "fp64_ms": ms64, "fp32_ms": ms32,
+           "fp64_mean_sweeps": float(sw64.double().mean()), "fp32_mean_sweeps": float(sw32.double().mean()),
+           "converged": int((info64 == 0).sum()) + int((info32 == 0).sum()),
+           "workload": "2048 FP64 of order uniform in {32..256} + 4096 FP32 of order uniform in {8..128}, "
+                       "Q1 diag(sigma) Q2^T; forward and dA = U diag(dS) V^T through the autograd Function"}
+    del parts
+    torch.cuda.empty_cache()
+    return out
+
+
+def narrow_leg(steps, warmup, dev, D):
+    """The plain forward on 2^20 FP64 narrow-range matrices (exponents in [-20, 20], 25% upper
+    triangular, 5% with a zero row or column) through k2svd_dgesvd2.  The 112 MB of inputs and
+    outputs fit in L2, so a 512 MB buffer is written between timed calls (outside the events)."""
+    import torch
+    from paper_2407_13116_gb300 import inputs as I
+    from paper_2407_13116_gb300 import k2svd
+    n = 1 << 20
+    G = I.general(n, SEED + 1, "d", "narrow", i0=shard_offset(n, D.rank), xp="torch", device=dev)
+    U = torch.empty((4, n), dtype=torch.float64, device=dev); V = torch.empty_like(U)
+    S = torch.empty((2, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(1 << 26, dtype=torch.float64, device=dev)
+    for _ in range(warmup):
+        k2svd.gesvd2(G, U=U, V=V, S=S, want_info=False)
+    ts = []
+    D.barrier()
+    for _ in range(max(steps, 10)):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        k2svd.gesvd2(G, U=U, V=V, S=S, want_info=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = D.max(statistics.median(ts))
+    del G, U, V, S, flush
+    torch.cuda.empty_cache()
+    return {"value": D.world * n / (ms / 1e3), "unit": "SVDs/s", "ms": ms, "l2": "flushed between calls",
+            "workload": "2^20 FP64 narrow-range general matrices (25% triangular, 5% with a zero row or column)"}
 
 
 def phases_leg(steps, warmup, dev, D, rates, clk_mhz, oc):
@@ -608,26 +863,40 @@ def rect_leg(steps, warmup, dev, D, rates, clk_mhz):
                         "QR with column pivoting, the n x n Kogbetliantz driver, U = Q U_R"}
 
 
+def host_bytes():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        return 0
+
+
 def e2e_leg(steps, warmup, dev, D):
-    """End to end through the Python API: pinned host inputs -> device -> kernels -> host
-    outputs, in chunks over three streams with a buffer set each, so that the host-to-device
-    copy of one chunk, the kernel of another and the device-to-host copy of a third run at
-    the same time (ordering only within a stream; all streams join at the end of a step)."""
+    """End to end through the Python API on the headline batch: pinned host inputs ->
+    device -> kernels -> host outputs, in chunks over three streams with a buffer set each,
+    so that the host-to-device copy of one chunk, the kernels of another and the
+    device-to-host copy of a third run at the same time (ordering only within a stream; all
+    streams join at the end of a step).  Every copy and kernel of every chunk is bracketed
+    by CUDA events on its stream, so a slow step can be traced to the operation that was
+    slow."""
     import torch
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
     torch.cuda.empty_cache()          # the earlier legs' cached blocks go back to the driver
     n, c = E2E_HALF, E2E_CHUNK
+    # pinned host memory for inputs and outputs: 27 doubles per general + triangular pair
+    need = 2 * n * 27 * 8
+    if host_bytes() and need > 0.5 * host_bytes():
+        while n > c and 2 * n * 27 * 8 > 0.5 * host_bytes():
+            n //= 2
     nc = n // c
     dt = torch.float64
     NS = 3
-
-    def chunked(x):       # (k, n) -> (nc, k, c): every chunk one contiguous block
-        return x.reshape(x.shape[0], nc, c).permute(1, 0, 2).contiguous()
-
     i0 = shard_offset(n, D.rank)
-    Gh = chunked(I.general(n, SEED + 2, "d", "wide", i0=i0, xp="torch", device=dev)).cpu().pin_memory()
-    Th = chunked(I.triangular(n, SEED + 3, "d", "wide", i0=i0, xp="torch", device=dev)).cpu().pin_memory()
+    Gh = torch.empty((nc, 4, c), dtype=dt, pin_memory=True)
+    Th = torch.empty((nc, 3, c), dtype=dt, pin_memory=True)
+    for q in range(nc):              # generated on the device chunk by chunk, kept in host memory
+        Gh[q].copy_(I.general(c, SEED + 2, "d", "wide", i0=i0 + q * c, xp="torch", device=dev))
+        Th[q].copy_(I.triangular(c, SEED + 3, "d", "wide", i0=i0 + q * c, xp="torch", device=dev))
     outs = {k: torch.empty((nc, rows, c), dtype=dt, pin_memory=True) for k, rows in
             (("Ug", 4), ("Vg", 4), ("Sg", 2), ("Ut", 4), ("Vt", 4), ("St", 2))}
     streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
@@ -637,40 +906,59 @@ def e2e_leg(steps, warmup, dev, D):
                      "U": torch.empty((4, c), dtype=dt, device=dev), "V": torch.empty((4, c), dtype=dt, device=dev),
                      "S": torch.empty((2, c), dtype=dt, device=dev)})
     main = torch.cuda.current_stream()
+    ops = 2 * nc
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(ops)]
 
-    def step():
+    def step(record):
         for st in streams:
             st.wait_stream(main)
         j = 0
         for kind in ("g", "t"):
             for q in range(nc):
                 st, b = streams[j % NS], bufs[j % NS]
+                e = evs[j]
                 j += 1
                 with torch.cuda.stream(st):
+                    if record:
+                        e[0].record(st)
                     if kind == "g":
                         b["G"].copy_(Gh[q], non_blocking=True)
+                        if record:
+                            e[1].record(st)
                         k2svd.gesvd2(b["G"], U=b["U"], V=b["V"], S=b["S"], want_info=False)
                         U, V, S = outs["Ug"], outs["Vg"], outs["Sg"]
                     else:
                         b["T"].copy_(Th[q], non_blocking=True)
+                        if record:
+                            e[1].record(st)
                         k2svd.trsvd2(b["T"][0], b["T"][1], b["T"][2], U=b["U"], V=b["V"], S=b["S"], want_info=False)
                         U, V, S = outs["Ut"], outs["Vt"], outs["St"]
+                    if record:
+                        e[2].record(st)
                     U[q].copy_(b["U"], non_blocking=True)
                     V[q].copy_(b["V"], non_blocking=True)
                     S[q].copy_(b["S"], non_blocking=True)
+                    if record:
+                        e[3].record(st)
         for st in streams:
             main.wait_stream(st)
         torch.cuda.synchronize()
 
     for _ in range(warmup):
-        step()
+        step(False)
     D.barrier()
     t = time.perf_counter()
-    per = []
+    per, worst = [], {"h2d": 0.0, "kernel": 0.0, "d2h": 0.0}
+    sums = {"h2d": 0.0, "kernel": 0.0, "d2h": 0.0}
     for _ in range(steps):
         t1 = time.perf_counter()
-        step()
+        step(True)
         per.append(time.perf_counter() - t1)
+        for e in evs:
+            for nm, (a, b) in (("h2d", (0, 1)), ("kernel", (1, 2)), ("d2h", (2, 3))):
+                ms = e[a].elapsed_time(e[b])
+                worst[nm] = max(worst[nm], ms)
+                sums[nm] += ms
     el = D.max((time.perf_counter() - t) / steps)
     h2d = (4 + 3) * 8 * n
     d2h = 2 * (4 + 4 + 2) * 8 * n
@@ -685,11 +973,16 @@ def e2e_leg(steps, warmup, dev, D):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(); fn(); e1.record(); torch.cuda.synchronize()
         link[name] = x.numel() * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del Gh, Th, outs, bufs, x, y
+    torch.cuda.empty_cache()
     return {"value": D.world * 2 * n / el, "unit": "SVDs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "batch": 2 * n, "ms_per_step": el * 1e3, "streams": NS, "chunk": c, "link": link,
             "copy_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6,
             "step_ms_min_max": [min(per) * 1e3, max(per) * 1e3],
-            "step_ms_median": statistics.median(per) * 1e3}
+            "step_ms_median": statistics.median(per) * 1e3,
+            "per_op_ms_mean": {k: v / (steps * ops) for k, v in sums.items()},
+            "per_op_ms_max": worst,
+            "note": "inputs and outputs in pinned host memory; the timed region holds every copy"}
 
 
 def cpu_baseline(seconds=10.0):
@@ -742,7 +1035,7 @@ def run_ours(a):
     B.build()
     from paper_2407_13116_gb300 import k2svd
     L = k2svd.lib()
-    rates = probe_rates(L)
+    rates = probe_rates(k2svd.probe_lib())
     oc = load_opcounts()
     res = leg("d", N_HALF_D, a.steps, a.warmup, dev, D, clocks_index=D.local)
     ms = D.max(res["ms"])
@@ -797,7 +1090,11 @@ def run_ours(a):
     if not a.no_rect:
         out["rect"] = rect_leg(max(1, a.steps // 5), 1, dev, D, rates, clk_mhz)
     if not a.no_kog:
-        out["kogbet"] = kog_leg(max(2, a.steps // 3), 1, dev, D)
+        out["kogbet"] = kog_leg(max(2, a.steps // 3), 1, dev, D, rates)
+    if not a.no_kog_grad:
+        out["kogbet_grad"] = kog_grad_leg(max(2, a.steps // 5), 1, dev, D)
+    if not a.no_narrow:
+        out["narrow"] = narrow_leg(a.steps, a.warmup, dev, D)
     if D.world == 1 and not a.no_e2e:
         out["e2e"] = e2e_leg(max(5, a.steps // 2), 1, dev, D)
     if D.rank == 0 and D.world == 1 and not a.no_cpu_baseline:
@@ -847,16 +1144,20 @@ def run_reference(a):
 
 
 def profile_case(a):
-    """A few launches of each 2x2 kernel on a small batch of the wide-range workload
-    (2^22 matrices by default: 470 MB of inputs and outputs in double, above L2), or one
-    persistent Kogbetliantz run over 304 FP64 matrices of the batched workload's order mix
-    (default block sizes, no graph: one launch per order bucket)."""
+    """A few launches of each kernel on a small case of its benchmark workload, for ncu
+    captures: the 2x2 kernels on 2^22 wide-range matrices (d, s; dn, sn: the variant with the
+    hypot that is not correctly rounded; 470 MB of inputs and outputs in double, above L2),
+    the complex kernel (z), lasv2 and the adjoint (misc: 2^22 matrices each), or one
+    persistent Kogbetliantz run over 608 FP64 matrices of the batched workload's order mix
+    (kog: one launch per order bucket; prints the rotation operations 8 n^3 per sweep, the
+    unit of its ceiling)."""
+    import numpy as np
     import torch
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
     dev = torch.device("cuda", 0)
+    n = a.profile_n
     if a.profile_case == "z":
-        n = a.profile_n
         G = torch.empty((8, n), dtype=torch.float64, device=dev)
         G[0::2] = I.general(n, SEED + 6, "d", "wide", xp="torch", device=dev)
         G[1::2] = I.general(n, SEED + 7, "d", "wide", xp="torch", device=dev)
@@ -866,16 +1167,33 @@ def profile_case(a):
         torch.cuda.synchronize()
         print("profile case z n=%d done" % n)
         return
+    if a.profile_case == "misc":
+        T3 = I.triangular(n, SEED + 3, "d", "wide", xp="torch", device=dev)
+        R, _, _ = I.rotated(n, SEED + 3)
+        G = torch.from_numpy(R).to(dev)
+        U, V, S, _, _, _ = k2svd.gesvd2(G, want_info=False)
+        gen = torch.Generator(device=dev).manual_seed(SEED + 3)
+        dS = torch.randn((2, n), dtype=torch.float64, device=dev, generator=gen)
+        dU = torch.randn((4, n), dtype=torch.float64, device=dev, generator=gen)
+        dV = torch.randn((4, n), dtype=torch.float64, device=dev, generator=gen)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            k2svd.lasv2(T3[0], T3[1], T3[2])
+            k2svd.gesvd2_bwd(U, S, V, dS, dU, dV)
+        torch.cuda.synchronize()
+        print("profile case misc n=%d done" % n)
+        return
     if a.profile_case == "kog":
-        orders = I.kog_orders(304, 8, 128, SEED + 4)
+        orders = I.kog_orders(608, 8, 128, SEED + 4)
         flat, _ = I.kog_batch(orders, SEED + 4)
         A = torch.from_numpy(flat).to(dev)
         U, S, V, sw, info = k2svd.kogbet(A, orders, flags=k2svd.KOG_NOTUNE)
         torch.cuda.synchronize()
-        print("profile case kog: %d matrices, mean sweeps %.2f, converged %d" %
-              (len(orders), sw.double().mean().item(), int((info == 0).sum().item())))
+        swn = sw.cpu().numpy().astype(np.int64)
+        rot = float((swn * 8 * orders.astype(np.int64) ** 3).sum())
+        print("profile case kog: %d matrices, mean sweeps %.2f, converged %d, rotation operations %.6g" %
+              (len(orders), swn.mean(), int((info == 0).sum().item()), rot))
         return
-    n = a.profile_n
     prec, ncr = a.profile_case[0], a.profile_case.endswith("n")
     G = I.general(n, SEED + 2, prec, "wide", xp="torch", device=dev)
     T3 = I.triangular(n, SEED + 3, prec, "wide", xp="torch", device=dev)
@@ -889,6 +1207,9 @@ def profile_case(a):
 
 def main():
     a = parse()
+    if a.summarize_ncu:
+        summarize_ncu(a.summarize_ncu, a.units)
+        return
     if a.profile_case:
         profile_case(a)
         return

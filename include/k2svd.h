@@ -10,8 +10,8 @@
  * Pointers.  Every array argument is a DEVICE pointer (cudaMalloc'd or managed
  *   memory), owned by the caller; the library never allocates, frees or keeps them.
  *   Optional arrays are marked "nullable" and are skipped when NULL.
- * Library memory.  Only k2svd_dgesvd2 on 65536 or more matrices allocates: stream-ordered
- *   scratch from a private pool (see there); k2svd_dkogbet_noalloc uses a static array.
+ * Library memory.  No entry point allocates device memory; scratch, where an entry point
+ *   needs it, is a caller-supplied workspace (k2svd_dkogbet_noalloc: a static array).
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *   stream).  Calls are asynchronous and stream-ordered; a return value of 0 means
  *   the work was enqueued.  Kernel faults surface as CUDA errors on that stream.
@@ -25,6 +25,14 @@
  * Errors.  Return 0 on success; -i when argument i (1-based) is invalid, checked in
  *   order, LAPACK style; K2SVD_ECUDA when a CUDA call failed (the CUDA error is left
  *   for cudaGetLastError to report).  Per-matrix conditions go to `info` (below).
+ * Graph capture.  The 2x2 entry points (k2svd_?gesvd2, k2svd_?trsvd2 and their variants,
+ *   k2svd_?gesvd2_bwd, k2svd_?prescale2, k2svd_?lasv2, k2svd_?gesvd2 of complex type) only
+ *   launch kernels on device pointers and may be captured into a CUDA graph.  The n x n
+ *   entry points (k2svd_?kogbet, k2svd_dkogbet_noalloc, k2svd_?kog_sigma_bwd,
+ *   k2svd_?gesvdr) copy a host-side table of the call to the device; a captured copy would
+ *   read that table at replay time, after it is gone, so they return K2SVD_ECAPTURE on a
+ *   stream that is being captured (K2SVD_KOG_GRAPH builds and caches a graph internally
+ *   instead).
  * Inputs must be finite (Sect. 2).  A matrix with a NaN or infinite element gets
  *   info = -1 and NaN in all its outputs; the other matrices are unaffected.
  */
@@ -39,6 +47,7 @@ extern "C" {
 #endif
 
 #define K2SVD_ECUDA (-1000)
+#define K2SVD_ECAPTURE (-1002)   /* the stream is being captured into a CUDA graph */
 
 /* info bits per matrix (when info != NULL and the input is finite):
  *   bits 0-3  zero-pattern type t of G (eq. (ts): 1 = g11, 2 = g21, 4 = g12, 8 = g22 non-zero)
@@ -75,11 +84,10 @@ extern "C" {
  *   stream  cudaStream_t as void*
  * Planes of different arrays must not overlap.  Argument order for error codes:
  * 1 batch, 2 G, 3 ldg, 4 U, 5 ldu, 6 V, 7 ldv, 8 S, 9 lds.
- * k2svd_dgesvd2 on 65536 or more matrices runs the method as two kernels (phases 1-2, then
- * phase 3) with their intermediate state in a scratch buffer of 48 bytes per matrix (at most
- * 2^24 matrices at a time, 805 MB), allocated in stream order on `stream` from a private
- * memory pool of the library that keeps up to 1 GiB between calls; if no scratch can be had
- * it runs the single fused kernel.  The results are the same bits either way.
+ * k2svd_dgesvd2 on 65536 or more matrices runs the method as two kernels per chunk of the
+ * batch (phases 1-2, then phase 3); between the two launches a matrix's intermediate state
+ * (48 bytes) is kept in its own U, V and S output planes, so the call needs no scratch
+ * memory.  The results are the same bits as the single fused kernel's.
  */
 int k2svd_dgesvd2(int64_t batch, const double *G, int64_t ldg,
                   double *U, int64_t ldu, double *V, int64_t ldv,
@@ -165,7 +173,8 @@ int k2svd_strsvd2_ncr(int64_t batch, const float *F, const float *Gu, const floa
  *                    k2svd_?gesvdr_ws for the same batch, m, n and flags; owned by the caller
  * Argument order for error codes: 1 batch, 2 m, 3 n, 4 aoffs, 5 uoffs, 6 voffs, 7 soffs,
  * 8 A, 9 U, 10 V, 11 S, 14 max_sweeps, 15 tol_factor, 16 flags, 17 workspace, 18 ws_bytes;
- * -19 when the square driver rejects the reduced problem; K2SVD_ECUDA for CUDA errors.
+ * -19 when the square driver rejects the reduced problem; K2SVD_ECUDA for CUDA errors;
+ * K2SVD_ECAPTURE on a stream that is being captured into a CUDA graph.
  */
 int k2svd_dgesvdr_ws(int64_t batch, const int32_t *m, const int32_t *n, int32_t flags, size_t *ws_bytes);
 int k2svd_sgesvdr_ws(int64_t batch, const int32_t *m, const int32_t *n, int32_t flags, size_t *ws_bytes);
@@ -322,6 +331,8 @@ int k2svd_sgesvd2_bwd(int64_t batch, const float *U, const float *S, const float
  *   workspace    device scratch of ws_bytes bytes, 256-byte aligned, from k2svd_?kogbet_ws
  *                for the same batch, n and flags; owned by the caller, not kept after the call
  *                (a cached graph refers to it: keep it alive while reusing the same arguments)
+ * Returns K2SVD_ECAPTURE when `stream` is being captured into a CUDA graph (the call copies
+ * its host-side descriptor table; use K2SVD_KOG_GRAPH for a graph launch).
  * The persistent form groups the matrices by order into buckets; each bucket runs as one
  * persistent launch (one CTA per matrix at a time, longest first, G in shared memory up to
  * order 128 for double and 224 for float, else in the workspace), with the block size
@@ -348,9 +359,9 @@ int k2svd_skogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
  * k2svd_dkogbet_noalloc -- k2svd_dkogbet for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a service entry point.  Some callers may not
  * allocate at all: a host whose device memory is entirely owned by another allocator (a
- * framework's caching allocator that reserved it up front), a latency-critical path in
- * which an allocation could block or fail, or a plugin that has no access to the
- * allocator.  This entry needs no workspace: its scratch (the work queues, the descriptor
+ * framework's caching allocator that reserved it up front), a path that must not fail on
+ * an allocation, or a plugin that has no access to the allocator.  This entry needs no
+ * workspace: its scratch (the work queues, the descriptor
  * table and, for orders above 128, the working copies of G) lives in one static device
  * array of K2SVD_KOG_NOALLOC_BYTES bytes that every GPU holds from the time it loads the
  * library until the process exits.  The call makes no device or host heap allocation.
@@ -362,7 +373,10 @@ int k2svd_skogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
  *   each order n above 128, each part rounded up to 256 bytes, plus 512 bytes (so up to
  *   32752 matrices of orders <= 128).
  *   The first call on a device looks up the address of that device's array with the device
- *   current; make that first call before any stream capture.
+ *   current.  The call uploads its descriptor table from a static host array with a
+ *   cudaMemcpyAsync from pageable memory, which CUDA performs synchronously with respect to
+ *   the host: the call returns only after the work already queued on `stream` has finished.
+ *   The call cannot be captured into a CUDA graph (K2SVD_ECAPTURE).
  *   All calls share the array and each call overwrites it: calls whose work overlaps on a
  *   GPU (other streams, other host threads) race.  Serialize them, e.g. on one stream.
  */
@@ -381,7 +395,7 @@ int k2svd_dkogbet_noalloc(int64_t batch, const int32_t *n, const int64_t *offs, 
  * fma (bitwise reproducible).  batch <= 65535.  workspace: device scratch of at least
  * 32 * batch bytes, 256-byte aligned (the k2svd_?kogbet workspace is large enough).
  * Argument order for error codes: 1 batch, 2 n, 3 offs, 4 soffs, 5 U, 6 V, 7 dS, 8 dA,
- * 9 workspace, 10 ws_bytes.
+ * 9 workspace, 10 ws_bytes.  K2SVD_ECAPTURE on a stream that is being captured.
  */
 int k2svd_dkog_sigma_bwd(int64_t batch, const int32_t *n, const int64_t *offs, const int64_t *soffs,
                          const double *U, const double *V, const double *dS, double *dA,

@@ -170,13 +170,37 @@ __device__ __forceinline__ void kog_rotate_g(T *G, int ld, int n, int st, const 
 }
 
 // U and V updates of step st (columns i, j of U <- U-hat, of V <- V-hat) by threads
-// t0, t0+tn, ...
+// t0, t0+tn, ...  U and V live in global memory (L2), so each thread takes two items at a
+// time and issues all eight loads before any arithmetic: the items touch distinct elements
+// (the pairs of a step are disjoint), and two L2 round trips overlap instead of following
+// one another.
 template <typename T>
 __device__ __forceinline__ void kog_rotate_uv(T *U, T *V, int n, int st, const T *piv, int ps, int t0, int tn)
 {
     const int np = modulus_count(n, st);
     const int items = np * n;
-    for (int w = t0; w < items; w += tn) {
+    int w = t0;
+#ifndef K2_KOG_UV_NOPREFETCH
+    for (; w + tn < items; w += 2 * tn) {
+        const int w1 = w + tn;
+        const int r0 = w % n, p0 = w / n, r1 = w1 % n, p1 = w1 / n;
+        int i0, j0, i1, j1;
+        modulus_pair(n, st, p0, i0, j0);
+        modulus_pair(n, st, p1, i1, j1);
+        T *ua0 = U + (size_t)i0 * n + r0, *ub0 = U + (size_t)j0 * n + r0;
+        T *va0 = V + (size_t)i0 * n + r0, *vb0 = V + (size_t)j0 * n + r0;
+        T *ua1 = U + (size_t)i1 * n + r1, *ub1 = U + (size_t)j1 * n + r1;
+        T *va1 = V + (size_t)i1 * n + r1, *vb1 = V + (size_t)j1 * n + r1;
+        T x0 = *ua0, y0 = *ub0, s0 = *va0, t0v = *vb0, x1 = *ua1, y1 = *ub1, s1 = *va1, t1v = *vb1;
+        rot2(x0, y0, piv + p0, ps);
+        rot2(s0, t0v, piv + 4 * ps + p0, ps);
+        rot2(x1, y1, piv + p1, ps);
+        rot2(s1, t1v, piv + 4 * ps + p1, ps);
+        *ua0 = x0; *ub0 = y0; *va0 = s0; *vb0 = t0v;
+        *ua1 = x1; *ub1 = y1; *va1 = s1; *vb1 = t1v;
+    }
+#endif
+    for (; w < items; w += tn) {
         const int r = w % n, p = w / n;
         int i, j;
         modulus_pair(n, st, p, i, j);
@@ -222,12 +246,17 @@ __device__ __forceinline__ void kog_step(T *G, int ld, T *U, T *V, int n, int st
             g12 = kog_next_entry(G, ld, n, st, pc, ps, i, j);
             g22 = kog_next_entry(G, ld, n, st, pc, ps, j, j);
         }
+#ifdef K2_KOG_REORDER
+        else if (tid >= w0) kog_rotate_uv(U, V, n, st, pc, ps, tid - w0, blockDim.x - w0);
+#endif
         __syncthreads();                                    // G_k read before phase 1 writes
         if (tid < w0) {
             if (tid < npn) kog_pivot(g11, g21, g12, g22, pn + tid, ps);
         } else {
             kog_rotate_g(G, ld, n, st, pc, ps, tid - w0, blockDim.x - w0);
+#ifndef K2_KOG_REORDER
             kog_rotate_uv(U, V, n, st, pc, ps, tid - w0, blockDim.x - w0);
+#endif
         }
     } else {
         kog_rotate_g(G, ld, n, st, pc, ps, tid, blockDim.x);
@@ -288,6 +317,10 @@ __device__ void kog_fail(T *U, T *V, T *S, int n)
 // ---------------------------------------------------------------------------------------
 // persistent kernel
 // ---------------------------------------------------------------------------------------
+#ifndef K2_TUNE_PER_SM
+#define K2_TUNE_PER_SM 4
+#endif
+
 template <typename T, bool GG>
 __global__ void __launch_bounds__(512) kog_persistent(const kog_params<T> P)
 {
@@ -776,15 +809,26 @@ template <typename T> struct kog_limits;
 template <> struct kog_limits<double> { static constexpr int SMEM_MAX_N = 128; };
 template <> struct kog_limits<float> { static constexpr int SMEM_MAX_N = 224; };
 
+// Order buckets, one persistent launch each: orders up to 32, 48, ..., 128 (G in shared
+// memory), up to the shared-memory limit, and the rest (G in the workspace).  A bucket's
+// shared memory is sized by its largest order, so narrow buckets let several CTAs share an
+// SM where G is small: while one matrix waits on the serial 2x2 SVDs of its next step,
+// another's rotations use the FP64 pipe.
+static constexpr int BUCKET_TOP[] = {32, 48, 64, 80, 96, 112, 128};
+static constexpr int NFIXED = 7;
+static constexpr int NBUCKETS = NFIXED + 2;
+static constexpr int BUCKET_GLOBAL = NBUCKETS - 1;
+// the work counters of the buckets, QUEUE_STRIDE ints apart in the first 512 bytes of the scratch
+static constexpr int QUEUE_STRIDE = 8;
+static_assert(NBUCKETS * QUEUE_STRIDE <= 128, "bucket work counters exceed their 512 bytes");
+
 static int bucket_of(int n, int smem_max)
 {
-    if (n <= 32) return 0;
-    if (n <= 64) return 1;
-    if (n <= 128) return 2;
-    if (n <= smem_max) return 3;
-    return 4;
+    if (n <= smem_max)
+        for (int b = 0; b < NFIXED; ++b)
+            if (n <= BUCKET_TOP[b]) return b;
+    return n <= smem_max ? NFIXED : BUCKET_GLOBAL;
 }
-static constexpr int NBUCKETS = 5;
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -827,7 +871,7 @@ static int make_plan(int64_t batch, const int32_t *n, const int64_t *offs, const
     // persistent form, then the n(n-1)/2 pair weights of every matrix with the dynamic ordering
     int64_t g = 0;
     for (auto &d : pl.desc) {
-        const bool gg = pl.plain || bucket_of(d.n, smax) == 4;
+        const bool gg = pl.plain || bucket_of(d.n, smax) == BUCKET_GLOBAL;
         if (gg || pl.dyn) {
             d.goff = g;
             if (gg) g += ((int64_t)d.n * d.n + 1) & ~(int64_t)1;
@@ -895,7 +939,7 @@ static cudaError_t launch_bucket_k(const kog_params<T> &Pin, int threads, cudaSt
 template <typename T>
 static cudaError_t launch_bucket(const kog_params<T> &P, int bucket, bool dyn, int threads, cudaStream_t st, int *queue_dev)
 {
-    if (bucket == 4)
+    if (bucket == BUCKET_GLOBAL)
         return dyn ? launch_bucket_k<T, true, true>(P, threads, st, queue_dev) : launch_bucket_k<T, true, false>(P, threads, st, queue_dev);
     return dyn ? launch_bucket_k<T, false, true>(P, threads, st, queue_dev) : launch_bucket_k<T, false, false>(P, threads, st, queue_dev);
 }
@@ -912,7 +956,7 @@ static cudaError_t launch_persistent(const kog_plan<T> &pl, kog_params<T> base, 
         kog_params<T> P = base;
         P.desc = ddesc + pl.bstart[b];
         P.count = cnt;
-        P.queue = queues + 16 * b;
+        P.queue = queues + QUEUE_STRIDE * b;
         P.nmax = pl.bnmax[b];
         cudaError_t e = launch_bucket<T>(P, b, pl.dyn, threads[b], st, P.queue);
         if (e != cudaSuccess) return e;
@@ -942,8 +986,8 @@ static int autotune(const kog_plan<T> &pl, const kog_params<T> &base, cudaStream
         const int cand[5] = {32, 64, 128, 256, 512};
         kog_params<T> P = base;
         P.desc = reinterpret_cast<const kog_desc *>(ws + pl.off_desc) + pl.bstart[b];
-        P.count = std::min(cnt, 2 * sms);
-        P.queue = reinterpret_cast<int *>(ws + pl.off_queue) + 16 * b;
+        P.count = std::min(cnt, K2_TUNE_PER_SM * sms);
+        P.queue = reinterpret_cast<int *>(ws + pl.off_queue) + QUEUE_STRIDE * b;
         P.nmax = pl.bnmax[b];
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return K2SVD_ECUDA;
@@ -1052,6 +1096,7 @@ static int kogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
     if (rc) return rc;
     if (ws_bytes < pl.total) return -15;
     cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = capture_guard(st)) != 0) return rc;
     unsigned char *ws = static_cast<unsigned char *>(workspace);
     if (cudaMemcpyAsync(ws + pl.off_desc, pl.desc.data(), pl.desc.size() * sizeof(kog_desc), cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
@@ -1134,6 +1179,7 @@ static int kog_sigma_bwd(int64_t batch, const int32_t *n, const int64_t *offs, c
         nmax = std::max(nmax, (int)n[i]);
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = capture_guard(st)) return rc;
     kog_desc *d_desc = static_cast<kog_desc *>(workspace);
     if (cudaMemcpyAsync(d_desc, desc.data(), desc.size() * sizeof(kog_desc), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return K2SVD_ECUDA;
@@ -1183,13 +1229,15 @@ static int kogbet_noalloc(int64_t batch, const int32_t *n, const int64_t *offs, 
     if (!S) return -8;
     if (max_sweeps < 0) return -11;
     if (!(tol_factor > 0)) return -12;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = capture_guard(st)) return rc;
     const int smax = kog_limits<double>::SMEM_MAX_N;
     // scratch layout as the workspace of the persistent form: queues, descriptors, G of orders > 128
     size_t bytes = align256(128 * sizeof(int)) + align256((size_t)batch * sizeof(kog_desc));
     int64_t g = 0;
     for (int64_t i = 0; i < batch; ++i) {
         if (n[i] < 1 || n[i] > 4096) return -2;
-        if (bucket_of(n[i], smax) == 4) g += ((int64_t)n[i] * n[i] + 1) & ~(int64_t)1;
+        if (bucket_of(n[i], smax) == BUCKET_GLOBAL) g += ((int64_t)n[i] * n[i] + 1) & ~(int64_t)1;
     }
     bytes += align256((size_t)g * sizeof(double));
     if (bytes > (size_t)K2SVD_KOG_NOALLOC_BYTES) return K2SVD_ENOSPACE;
@@ -1213,7 +1261,7 @@ static int kogbet_noalloc(int64_t batch, const int32_t *n, const int64_t *offs, 
         int b = bucket_of(desc[i].n, smax);
         pl.bstart[b + 1] = (int)i + 1;
         pl.bnmax[b] = std::max(pl.bnmax[b], desc[i].n);
-        if (b == 4) { desc[i].goff = goff; goff += ((int64_t)desc[i].n * desc[i].n + 1) & ~(int64_t)1; }
+        if (b == BUCKET_GLOBAL) { desc[i].goff = goff; goff += ((int64_t)desc[i].n * desc[i].n + 1) & ~(int64_t)1; }
     }
     for (int b = 1; b <= NBUCKETS; ++b) pl.bstart[b] = std::max(pl.bstart[b], pl.bstart[b - 1]);
     pl.off_queue = 0;
@@ -1221,7 +1269,6 @@ static int kogbet_noalloc(int64_t batch, const int32_t *n, const int64_t *offs, 
     pl.off_g = pl.off_desc + align256((size_t)batch * sizeof(kog_desc));
     pl.plain = false;
     pl.dyn = false;
-    cudaStream_t st = (cudaStream_t)stream;
     unsigned char *ws = static_cast<unsigned char *>(scratch);
     if (cudaMemcpyAsync(ws + pl.off_desc, desc, (size_t)batch * sizeof(kog_desc), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return K2SVD_ECUDA;

@@ -286,6 +286,7 @@ static int gesvdr(int64_t batch, const int32_t *m, const int32_t *n, const int64
         d.aoff = aoffs[i]; d.uoff = uoffs[i]; d.voff = voffs[i]; d.soff = soffs[i];
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = capture_guard(st)) != 0) return rc;
     unsigned char *ws = static_cast<unsigned char *>(workspace);
     if (cudaMemcpyAsync(ws + pl.off_desc, pl.desc.data(), pl.desc.size() * sizeof(rect_desc), cudaMemcpyHostToDevice,
                         st) != cudaSuccess)
