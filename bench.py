@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--no-narrow", action="store_true")
     p.add_argument("--summarize-ncu", default=None, help="print per-pipe counts per unit from an ncu --csv log")
     p.add_argument("--units", default="", help="with --summarize-ncu: substring=units per launch, ...")
-    p.add_argument("--profile-case", choices=["d", "s", "dn", "sn", "kog", "z", "misc"], default=None,
+    p.add_argument("--profile-case", choices=["d", "s", "dn", "sn", "kog", "kog128", "z", "misc"], default=None,
                    help="run a small case of the 2x2 kernels (d, s; dn, sn: the variant with the hypot "
                         "that is not correctly rounded), of the complex kernel (z) or of the persistent "
                         "Kogbetliantz kernel (kog), for ncu captures, and exit")
@@ -185,19 +185,56 @@ PIPE_METRIC = {"issue": "sm__inst_executed", "fp64": "sm__inst_executed_pipe_fp6
 PIPE_PEAK = {"issue": 4.0, "fp64": 1.0 / 16, "alu": 2.0, "fmaheavy": 2.0, "fmalite": 2.0, "fma": 4.0,
              "lsu": 1.0, "xu": 1.0, "cbu": 4.0, "adu": 0.5, "uniform": 2.0}
 SRC_2X2 = ("k2_fp.cuh", "k2_svd2.cuh", "k2_svd2_kernel.cuh", "k2_gesvd2.cu")
-SRC_GROUPS = {"2x2": SRC_2X2, "complex": SRC_2X2 + ("k2_complex.cu",), "bwd": ("k2_bwd.cu",),
+SRC_GROUPS = {"2x2": SRC_2X2, "complex": SRC_2X2 + ("k2_complex.cu",), "bwd": ("k2_fp.cuh", "k2_bwd.cu"),
               "kog": SRC_2X2 + ("k2_kog.cu", "k2_kog_dev.cuh")}
-# kernel -> (source group, unit, {pipe: warp instructions per unit}, DRAM bytes per unit)
-PIPE_COUNTS_HASH = {}
-PIPE_COUNTS = {}
+# The source hashes at which the count tables below were taken (profiles/pipe_ceilings.md).
+PIPE_COUNTS_HASH = {"2x2": "577b077599ba4a63", "complex": "0924564194c96378", "bwd": "f51322056ad56ee9",
+                    "kog": "e4d709a5eaa858fe"}
+
+
+def _pc(group, unit, counts, dram):
+    return (group, unit, dict(zip(("issue", "fp64", "alu", "fmaheavy", "fmalite", "fma", "lsu", "xu", "cbu",
+                                   "adu", "uniform"), counts)), dram)
+
+
+# kernel -> (source group, unit, {pipe: warp instructions per unit}, DRAM bytes per unit under
+# ncu, caches flushed before each launch); 2^22-matrix captures of the benchmark workloads
+PIPE_COUNTS = {
+    "svd2a_kernel<double>": _pc("2x2", "matrix", (80.612, 1.3574, 43.827, 15.156, 1.5589, 16.715, 2.4225, 1.1828,
+                                                  6.5166, 0.26554, 0.0023193), 113.22),
+    "svd2b_kernel<double>": _pc("2x2", "matrix", (121.92, 1.3503, 56.488, 28.429, 2.9762, 31.406, 9.0118, 1.9121,
+                                                  11.736, 0.63089, 0.12732), 135.11),
+    "svd2_kernel<double,tri>": _pc("2x2", "matrix", (105.94, 1.4394, 49.661, 26.934, 2.4759, 29.41, 2.9868, 1.6091,
+                                                     11.059, 0.46691, 0.12732), 102.5),
+    "svd2_kernel<float,general>": _pc("2x2", "matrix", (85.492, 0.53125, 36.175, 18.157, 7.3987, 25.555, 1.6011,
+                                                        2.2688, 9.3348, 0.59087, 0.12732), 46.698),
+    "svd2_kernel<float,tri>": _pc("2x2", "matrix", (53.349, 0.0, 23.397, 10.942, 4.765, 15.707, 0.93654, 1.2987,
+                                                    6.432, 0.31998, 0.12732), 39.785),
+    "lasv2_kernel<double>": _pc("2x2", "matrix", (103.35, 1.4707, 49.69, 24.939, 2.4763, 27.416, 2.4509, 1.6091,
+                                                  11.184, 0.46695, 0.0023193), 72.12),
+    "csvd2_kernel<double>": _pc("complex", "matrix", (270.06, 4.2253, 119.46, 69.961, 6.1946, 76.155, 11.048, 4.0908,
+                                                      26.255, 1.3183, 0.083496), 634.61),
+    "bwd_kernel<double>": _pc("bwd", "matrix", (16.355, 1.2188, 5.5112, 2.6453, 0.21848, 2.8638, 0.75116, 0.125,
+                                                1.0449, 0.034565, 0.12616), 188.63),
+    "kog_persistent<double>": _pc("kog", "rotation FP64 operation", (0.59587, 0.035221, 0.17541, 0.14531, 0.0040116,
+                                                                     0.14932, 0.055805, 0.0065938, 0.027849,
+                                                                     0.0027299, 0.012637), 0.0010445),
+}
 
 
 def src_hash(group):
+    """Hash of the code of a group of kernel sources, comments and blank space removed (a
+    comment edit does not invalidate a count table)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in SRC_GROUPS[group]:
-        with open(os.path.join(ROOT, "paper_2407_13116_gb300", "csrc", f), "rb") as fh:
-            h.update(hashlib.sha256(fh.read()).hexdigest().encode() + b"  " + f.encode() + b"\n")
+        with open(os.path.join(ROOT, "paper_2407_13116_gb300", "csrc", f)) as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        code = " ".join(code.split())
+        h.update(hashlib.sha256(code.encode()).hexdigest().encode() + b"  " + f.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
@@ -494,15 +531,8 @@ def fwd_bwd_leg(steps, warmup, dev, D, rates, clk_mhz):
     t_fp64, t_hbm = n * ops / peak, bwd_bytes / (hbm * 1e9)
     return {"value": D.world * n / (ms / 1e3), "unit": "fwd+bwd/s", "matrices_per_gpu_per_step": n,
             "fwd_ms": fwd, "bwd_ms": bwd, "bwd_over_fwd": bwd / fwd,
-            "bwd_roofline": {"bound": "alu" if t_fp64 > t_hbm else "hbm",
-                             "achieved": n * ops / (bwd / 1e3) / 1e9, "peak": peak / 1e9,
-                             "unit": "G FP64-pipe op/s", "frac": (n * ops / (bwd / 1e3)) / peak,
-                             "ops_per_matrix": ops, "algorithmic_bytes": bwd_bytes,
-                             "hbm_frac": bwd_bytes / (bwd / 1e3) / (hbm * 1e9), "hbm_peak_gbs": hbm,
-                             "hbm_peak_source": hbm_src,
-                             "note": "the lesser of HBM (192 B/matrix) and the FP64 pipe over the adjoint's "
-                                     "operations, the division at its FP64-pipe cost; the kernel divides on "
-                                     "the integer pipes"},
+            "bwd_roofline": roofline_entry(["bwd_kernel<double>"], n, "matrix", bwd / 1e3, clk_mhz, bwd_bytes,
+                                           fp64_model=(n * ops / (bwd / 1e3)) / peak),
             "workload": "2^24 FP64 R(theta) diag(s1,s2) R(phi)^T, 10% near-equal singular values, upstream N(0,1)"}
 
 
@@ -606,7 +636,7 @@ def kog_leg(steps, warmup, dev, D, rates):
     # BASELINE's FP64 model: per sweep n(n-1)/2 pivots at 239 FP64 slots and 16 n FP64
     # operations per pivot for the rotations
     ops = float((sweeps * (nn * (nn - 1) // 2) * (16 * nn + 239)).sum())
-    roof = roofline_entry(["kog_persistent"], float(rot.sum()), "rotation FP64 op", pers_ms / 1e3, clk_mhz, None,
+    roof = roofline_entry(["kog_persistent<double>"], float(rot.sum()), "rotation FP64 op", pers_ms / 1e3, clk_mhz, None,
                           fp64_model=ops / (pers_ms / 1e3) / nominal)
     roof["unit_note"] = ("units are the rotations' FP64 operations (8 n^3 per sweep); the ceiling scales the "
                          "instructions counted per such operation on a 608-matrix sample of the same order mix")
@@ -753,9 +783,8 @@ def phases_leg(steps, warmup, dev, D, rates, clk_mhz, oc):
     cost = slot_costs(oc["wide_d_trsvd2"], rates, "d")["fp64"]
     peak = fp64_peak(clk_mhz)
     res["lasv2"] = {"value": D.world * n / (ms / 1e3), "unit": "SVDs/s", "ms": ms,
-                    "roofline": {"bound": "alu", "achieved": n * cost / (ms / 1e3) / 1e9, "peak": peak / 1e9,
-                                 "unit": "G FP64-pipe op/s", "frac": n * cost / (ms / 1e3) / peak,
-                                 "ops_per_matrix": cost, "algorithmic_bytes": 72 * n},
+                    "roofline": roofline_entry(["lasv2_kernel<double>"], n, "SVD", ms / 1e3, clk_mhz, 72 * n,
+                                               fp64_model=n * cost / (ms / 1e3) / peak),
                     "workload": "2^27 wide-range FP64 upper-triangular matrices (F, G, H in, 6 planes out)"}
     del T3, outs
     torch.cuda.empty_cache()
@@ -794,9 +823,8 @@ def complex_leg(steps, warmup, dev, D, rates, clk_mhz, oc):
     del G, U, V, S
     torch.cuda.empty_cache()
     return {"value": D.world * n / (ms / 1e3), "unit": "SVDs/s", "ms": ms,
-            "roofline": {"bound": "alu", "achieved": n * cost / (ms / 1e3) / 1e9, "peak": peak / 1e9,
-                         "unit": "G FP64-pipe op/s", "frac": n * cost / (ms / 1e3) / peak, "ops_per_matrix": cost,
-                         "algorithmic_bytes": nbytes, "hbm_frac": nbytes / (ms / 1e3) / (hbm * 1e9)},
+            "roofline": roofline_entry(["csvd2_kernel<double>"], n, "SVD", ms / 1e3, clk_mhz, nbytes,
+                                       fp64_model=n * cost / (ms / 1e3) / peak),
             "workload": "2^26 double complex 2x2 matrices, real and imaginary parts wide-range (exponents "
                         "uniform in [-1021,1021], 2% subnormal or near-overflow); 208 B per matrix"}
 
@@ -1034,32 +1062,27 @@ def run_ours(a):
     from paper_2407_13116_gb300 import build as B
     B.build()
     from paper_2407_13116_gb300 import k2svd
-    L = k2svd.lib()
+    k2svd.lib()
     rates = probe_rates(k2svd.probe_lib())
     oc = load_opcounts()
     res = leg("d", N_HALF_D, a.steps, a.warmup, dev, D, clocks_index=D.local)
     ms = D.max(res["ms"])
     value = D.world * 2 * N_HALF_D / (ms / 1e3)
+    clk_mhz = (res["clocks"] or {}).get("sm_mhz") or 2070.0
+    # BASELINE's FP64-pipe model of the method's counted operations, kept beside the ceiling
     cost_ge = slot_costs(oc["wide_d_gesvd2"], rates, "d")["fp64"]
     cost_tr = slot_costs(oc["wide_d_trsvd2"], rates, "d")["fp64"]
-    ach = N_HALF_D * cost_ge / (res["ge_ms"] / 1e3)
-    clk_mhz = (res["clocks"] or {}).get("sm_mhz") or 2070.0
-    peak = fp64_peak(clk_mhz)
-    roof_step = 2 * N_HALF_D / ((N_HALF_D * (cost_ge + cost_tr)) / peak)
-    traffic = TRAFFIC_BYTES_PER_MATRIX * N_HALF_D if kernel_hash() == TRAFFIC_SRC_HASH else None
-    roofline = {"bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9,
-                "unit": "G FP64-pipe op/s", "frac": ach / peak, "traffic": traffic,
-                "kernel": "svd2a_kernel + svd2b_kernel<double> (k2svd_dgesvd2: phases 1-2, then phase 3)",
-                "kernel_ms": res["ge_ms"], "ops_per_matrix": cost_ge,
-                "algorithmic_bytes": BYTES_GE["d"] * N_HALF_D,
-                "peak_source": "nominal: SMs x 2 DFMA/clk x median SM clock %.0f MHz during the timed region; "
-                               "live probe reached %.3g DFMA/s; divide %.2f, sqrt %.2f fma slots (probe)" % (
-                                   clk_mhz, rates["dfma"], rates["dfma"] / rates["ddiv"], rates["dfma"] / rates["dsqrt"]),
-                "step_frac": value / D.world / roof_step,
-                "note": "roofline of the method's counted operations (oracle counters) at their FP64-pipe issue "
-                        "cost, divisions and square roots weighted by the probe; the kernel runs the divisions, "
-                        "the hypot, comparisons and exact steps on the integer pipes, so it may pass this bound",
-                "hbm_bound_svds_per_s": 1e9 * hbm_peak_gbs()[0] / ((BYTES_GE["d"] + BYTES_TR["d"]) / 2)}
+    peak64 = fp64_peak(clk_mhz)
+    model_ge = N_HALF_D * cost_ge / (res["ge_ms"] / 1e3) / peak64
+    model_step = 2 * N_HALF_D / (ms / 1e3) / D.world / (2 * N_HALF_D / ((N_HALF_D * (cost_ge + cost_tr)) / peak64))
+    roofline = roofline_entry(["svd2a_kernel<double>", "svd2b_kernel<double>"], N_HALF_D, "SVD",
+                              res["ge_ms"] / 1e3, clk_mhz, BYTES_GE["d"] * N_HALF_D, fp64_model=model_ge)
+    roofline["entry"] = "k2svd_dgesvd2 (phases 1-2, then phase 3)"
+    tri = roofline_entry(["svd2_kernel<double,tri>"], N_HALF_D, "SVD", res["tr_ms"] / 1e3, clk_mhz,
+                         BYTES_TR["d"] * N_HALF_D)
+    c_step = ceiling(["svd2a_kernel<double>", "svd2b_kernel<double>", "svd2_kernel<double,tri>"], N_HALF_D, clk_mhz)
+    roofline["step"] = {"frac": (c_step[0] / (ms / 1e3)) if c_step else None, "fp64_model_frac": model_step,
+                        "trsvd2": tri}
     out = {"metric": METRIC, "value": value, "unit": "SVDs/s", "n_gpus": D.world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -1067,8 +1090,9 @@ def run_ours(a):
            "clocks": res["clocks"], "gpu_launches": res["launches"], "roofline": roofline,
            "pipe_rates": rates}
     if not a.no_fp32:
-        rs = leg("s", N_HALF_S, a.steps, a.warmup, dev, D)
+        rs = leg("s", N_HALF_S, a.steps, a.warmup, dev, D, clocks_index=D.local)
         mss = D.max(rs["ms"])
+        clk_s = (rs["clocks"] or {}).get("sm_mhz") or clk_mhz
         cs_ge = slot_costs(oc["wide_s_gesvd2"], rates, "s")
         cs_tr = slot_costs(oc["wide_s_trsvd2"], rates, "s")
         roof32 = 2 / ((cs_ge["fp32"] + cs_tr["fp32"]) / rates["ffma"])
@@ -1076,9 +1100,13 @@ def run_ours(a):
         roofhbm = 2 / ((BYTES_GE["s"] + BYTES_TR["s"]) / (hbm_peak_gbs()[0] * 1e9))
         vs = D.world * 2 * N_HALF_S / (mss / 1e3)
         out["fp32"] = {"value": vs, "unit": "SVDs/s", "ms_per_step": mss, "matrices_per_gpu_per_step": 2 * N_HALF_S,
-                       "roofline_svds_per_s": {"fp32_pipe": roof32, "fp64_pipe": roof64, "hbm": roofhbm},
-                       "frac_of_min_roofline": vs / D.world / min(roof32, roof64, roofhbm),
-                       "gesvd2_ms": rs["ge_ms"], "trsvd2_ms": rs["tr_ms"]}
+                       "gesvd2_ms": rs["ge_ms"], "trsvd2_ms": rs["tr_ms"], "clocks": rs["clocks"],
+                       "roofline": roofline_entry(["svd2_kernel<float,general>"], N_HALF_S, "SVD", rs["ge_ms"] / 1e3,
+                                                  clk_s, BYTES_GE["s"] * N_HALF_S),
+                       "roofline_trsvd2": roofline_entry(["svd2_kernel<float,tri>"], N_HALF_S, "SVD",
+                                                         rs["tr_ms"] / 1e3, clk_s, BYTES_TR["s"] * N_HALF_S),
+                       "fp32_model_frac": vs / D.world / min(roof32, roof64, roofhbm),
+                       "fp32_model_svds_per_s": {"fp32_pipe": roof32, "fp64_pipe": roof64, "hbm": roofhbm}}
     if not a.no_ncr:
         out["ncr"] = ncr_leg(a.steps, a.warmup, dev, D, rates, clk_mhz, oc, value, out.get("fp32"))
     if not a.no_fwd_bwd:
@@ -1183,8 +1211,8 @@ def profile_case(a):
         torch.cuda.synchronize()
         print("profile case misc n=%d done" % n)
         return
-    if a.profile_case == "kog":
-        orders = I.kog_orders(608, 8, 128, SEED + 4)
+    if a.profile_case in ("kog", "kog128"):
+        orders = I.kog_orders(608, 8, 128, SEED + 4) if a.profile_case == "kog" else np.full(304, 128, np.int32)
         flat, _ = I.kog_batch(orders, SEED + 4)
         A = torch.from_numpy(flat).to(dev)
         U, S, V, sw, info = k2svd.kogbet(A, orders, flags=k2svd.KOG_NOTUNE)

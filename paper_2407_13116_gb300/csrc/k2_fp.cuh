@@ -350,11 +350,10 @@ __device__ __forceinline__ uint64_t isqrt113(u128 X, u128 &rem)
 //  * e_a - e_b >= (p+1)/2: b^2 < a ulp(a), so sqrt(a^2+b^2) lies strictly inside
 //    (a, a + ulp(a)/2) and rounds to a;
 //  * otherwise the exact sum of squares X is formed as an integer (a' = a scaled to
-//    [1,2), units 2^-110 for double; both subnormal: units of the smallest subnormal
-//    squared) and the result is rounded from floor(sqrt X) and the remainder, ties to
-//    even.  The double version uses no FP64 instruction on this path.  For float, a
-//    candidate sqrt(fma(a', a', b'*b')) is corrected by comparing the exact a'^2 + b'^2 with
-//    the squared midpoints to the neighbouring values, in integers (units 2^-52).
+//    [1,2), units 2^-110 for double and 2^-52 for float; both subnormal: units of the
+//    smallest subnormal squared) and the result is rounded from floor(sqrt X) (isqrt113,
+//    isqrt55), the remainder and the truncated bits of b'^2, ties to even.  Neither version
+//    uses a floating-point square root, and the double one no FP64 instruction, on this path.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ double hypot_cr_body(double x, double y)
 {

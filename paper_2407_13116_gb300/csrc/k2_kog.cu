@@ -180,7 +180,6 @@ __device__ __forceinline__ void kog_rotate_uv(T *U, T *V, int n, int st, const T
     const int np = modulus_count(n, st);
     const int items = np * n;
     int w = t0;
-#ifndef K2_KOG_UV_NOPREFETCH
     for (; w + tn < items; w += 2 * tn) {
         const int w1 = w + tn;
         const int r0 = w % n, p0 = w / n, r1 = w1 % n, p1 = w1 / n;
@@ -199,7 +198,6 @@ __device__ __forceinline__ void kog_rotate_uv(T *U, T *V, int n, int st, const T
         *ua0 = x0; *ub0 = y0; *va0 = s0; *vb0 = t0v;
         *ua1 = x1; *ub1 = y1; *va1 = s1; *vb1 = t1v;
     }
-#endif
     for (; w < items; w += tn) {
         const int r = w % n, p = w / n;
         int i, j;
@@ -246,17 +244,12 @@ __device__ __forceinline__ void kog_step(T *G, int ld, T *U, T *V, int n, int st
             g12 = kog_next_entry(G, ld, n, st, pc, ps, i, j);
             g22 = kog_next_entry(G, ld, n, st, pc, ps, j, j);
         }
-#ifdef K2_KOG_REORDER
-        else if (tid >= w0) kog_rotate_uv(U, V, n, st, pc, ps, tid - w0, blockDim.x - w0);
-#endif
         __syncthreads();                                    // G_k read before phase 1 writes
         if (tid < w0) {
             if (tid < npn) kog_pivot(g11, g21, g12, g22, pn + tid, ps);
         } else {
             kog_rotate_g(G, ld, n, st, pc, ps, tid - w0, blockDim.x - w0);
-#ifndef K2_KOG_REORDER
             kog_rotate_uv(U, V, n, st, pc, ps, tid - w0, blockDim.x - w0);
-#endif
         }
     } else {
         kog_rotate_g(G, ld, n, st, pc, ps, tid, blockDim.x);
@@ -317,10 +310,6 @@ __device__ void kog_fail(T *U, T *V, T *S, int n)
 // ---------------------------------------------------------------------------------------
 // persistent kernel
 // ---------------------------------------------------------------------------------------
-#ifndef K2_TUNE_PER_SM
-#define K2_TUNE_PER_SM 4
-#endif
-
 template <typename T, bool GG>
 __global__ void __launch_bounds__(512) kog_persistent(const kog_params<T> P)
 {
@@ -965,7 +954,8 @@ static cudaError_t launch_persistent(const kog_plan<T> &pl, kog_params<T> base, 
 }
 
 // Pick the block size of each bucket by timing a sample (the largest matrices of the
-// bucket, two per SM) on the caller's arrays; results are launch-shape independent.
+// bucket, four per SM, so that a block size that fits several CTAs on an SM can show it)
+// on the caller's arrays; results are launch-shape independent.
 template <typename T>
 static int autotune(const kog_plan<T> &pl, const kog_params<T> &base, cudaStream_t st, unsigned char *ws, int dev,
                     int *threads, bool tune)
@@ -986,7 +976,7 @@ static int autotune(const kog_plan<T> &pl, const kog_params<T> &base, cudaStream
         const int cand[5] = {32, 64, 128, 256, 512};
         kog_params<T> P = base;
         P.desc = reinterpret_cast<const kog_desc *>(ws + pl.off_desc) + pl.bstart[b];
-        P.count = std::min(cnt, K2_TUNE_PER_SM * sms);
+        P.count = std::min(cnt, 4 * sms);
         P.queue = reinterpret_cast<int *>(ws + pl.off_queue) + QUEUE_STRIDE * b;
         P.nmax = pl.bnmax[b];
         cudaEvent_t e0, e1;

@@ -67,11 +67,7 @@ template <typename T>
 __device__ __forceinline__ void kog_pivot(T g11, T g21, T g12, T g22, T *m, int ps = 1)
 {
     svd2_out<T> o;
-#ifdef K2_KOG_PIVOT_FDIV
-    svd2<T, true>(g11, g21, g12, g22, o);
-#else
     svd2<T>(g11, g21, g12, g22, o);
-#endif
     m[0] = unneg0(o.U.a11); m[ps] = unneg0(o.U.a21); m[2 * ps] = unneg0(o.U.a12); m[3 * ps] = unneg0(o.U.a22);
     m[4 * ps] = unneg0(o.V.a11); m[5 * ps] = unneg0(o.V.a21); m[6 * ps] = unneg0(o.V.a12); m[7 * ps] = unneg0(o.V.a22);
     m[8 * ps] = ef_fl(o.s1);

@@ -124,18 +124,13 @@ static int launch(const svd_args<T> &a, cudaStream_t st)
 // ---------------------------------------------------------------------------------------
 constexpr int64_t SPLIT_MIN = 1 << 16;                    // smaller batches: the fused kernel
 
-// Which quotients use the FP64 divider (csdiv): the three of eq. (QR15) in phases 1-2, none
-// in phase 3.  Phases 1-2 are integer-heavy (the hypots, eq. (EXT)) and phase 3 FP64-heavy,
-// so the FP64 divider moves to the first half: on 2^26 wide-range matrices 19.1 ms against
-// 24.1 ms with the fused kernel's placement (the cos/sin quotients of Alg. 1 and 2 on the
-// divider), 20.0 with both, 20.3 with neither.
-#ifndef K2_SPLIT_FDIV_T
-#define K2_SPLIT_FDIV_T 1
-#endif
-#ifndef K2_SPLIT_FDIV_R
-#define K2_SPLIT_FDIV_R 1
-#endif
-constexpr bool SPLIT_FDIV_A = K2_SPLIT_FDIV_R, SPLIT_FDIV_AT = K2_SPLIT_FDIV_T, SPLIT_FDIV_B = false;
+// Which quotients use the FP64 divider (csdiv): r12 and r22 of eq. (QR15) in phases 1-2;
+// tan theta and every quotient of phase 3 on the integer pipes.  Phases 1-2 are
+// integer-heavy (the hypots, eq. (EXT)) and phase 3 FP64-heavy.  Measured on a GB300, 2^27
+// wide-range matrices (both halves): 32.8 ms, against 34.8 with tan theta also on the
+// divider, 34.0 with only tan theta on it and 33.2 with none (narrow-range 2^26: 22.8, 24.0,
+// 22.1, 22.0 ms).
+constexpr bool SPLIT_FDIV_A = true, SPLIT_FDIV_AT = false, SPLIT_FDIV_B = false;
 
 // The packed word in the sigma1 plane: bit 63 set (phase 3 pending); bits 0-3 t, 4-7 t',
 // 8-15 phase-1-2 flags, 16 c15, 17 pu, 18 pv, 19 na, 20 nb, 21 n12, 22 n22; bits 32-47 the

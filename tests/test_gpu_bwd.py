@@ -68,7 +68,9 @@ def _loss_gpu(G, dS, dU, dV):
             + (dV * V.cpu().numpy()).sum(axis=0))
 
 
-def _fd_gpu(G, dS, dU, dV, h):
+def _fd_gpu(G, dS, dU, dV, h, richardson=True):
+    """Central differences of the loss per matrix and element, divided by the step actually
+    taken (G[k] +- h rounded to a double); Richardson extrapolation over h and h/2."""
     out = np.zeros_like(G)
     for k in range(4):
         def d(hh):
@@ -76,16 +78,29 @@ def _fd_gpu(G, dS, dU, dV, h):
             Gp[k] += hh
             Gm[k] -= hh
             return (_loss_gpu(Gp, dS, dU, dV) - _loss_gpu(Gm, dS, dU, dV)) / ((Gp[k] - G[k]) + (G[k] - Gm[k]))
-        out[k] = (4 * d(h / 2) - d(h)) / 3
+        out[k] = (4 * d(h / 2) - d(h)) / 3 if richardson else d(h)
     return out
 
 
+def _rel(fd, an):
+    return np.sqrt(((fd - an) ** 2).sum(axis=0)) / np.sqrt((an ** 2).sum(axis=0))
+
+
 def test_finite_differences_4096():
-    """The differentiation workload: 4096 matrices R(theta) diag(s1, s2) R(phi)^T with 10% of
-    near-equal singular values.  Full loss (dS, dU, dV ~ N(0,1)) on the separated ones
-    (1e-3 < s2/s1 < 0.9, per-matrix step 1e-3 min(s2, s1 - s2)) to 1e-8 relative; the
-    singular-value loss on the others, to 1e-8 plus the rounding floor of a double central
-    difference (eps s1 / h)."""
+    """The differentiation workload: all 4096 matrices R(theta) diag(s1, s2) R(phi)^T
+    (s2/s1 log-uniform in [1e-12, 1], 10% within 1e-6 of 1), checked against central
+    differences of the GPU forward, each group with the loss and step its conditioning allows:
+      * 1e-3 < s2/s1 <= 1 - 2e-6: the full loss (dS, dU, dV ~ N(0,1)), step 1e-3 min(s2, s1 - s2),
+        to 1e-8 relative;
+      * s2/s1 > 1 - 2e-6 (near-equal, where U and V are ill-conditioned): the singular-value
+        loss, step 1e-2 (s1 - s2), to 1e-8 plus the rounding floor 200 eps s1 / h of a double
+        central difference;
+      * s2/s1 <= 1e-3: the singular-value loss, since any step above the rounding floor of U
+        and V is far above sigma2 and can flip the sign of det G, and with it the sign of the
+        second singular pair: sigma1 alone with step 1e-6 s1, and sigma2 alone with step
+        1e-3 s2 (a few ulps of the entries; the exact differences divide), each to 1e-8 plus
+        64 eps sigma_i / h -- the second holds only because the method computes a tiny sigma2
+        to a few ulps relative (Sect. 4)."""
     n = 4096
     G, s1, s2 = I.rotated(n, 0x240713116 + 3)
     U, V, S = _fwd(G)
@@ -94,27 +109,48 @@ def test_finite_differences_4096():
     rng = np.random.default_rng(4)
     dS, dU, dV = rng.standard_normal((2, n)), rng.standard_normal((4, n)), rng.standard_normal((4, n))
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
-    sep = (ratio > 1e-3) & (ratio < 0.9)
+    sep = (ratio > 1e-3) & (ratio <= 1 - 2e-6)
+    near = ratio > 1 - 2e-6
+    small = ratio <= 1e-3
+    assert (sep | near | small).all() and sep.sum() > 500 and near.sum() > 200 and small.sum() > 2000
+    # separated
     Gs = np.ascontiguousarray(G[:, sep])
     Us, Vs, Ss = _fwd(Gs)
     an = k2().gesvd2_bwd(Us, Ss, Vs, t(dS[:, sep]), t(dU[:, sep]), t(dV[:, sep])).cpu().numpy()
     S_s = Ss.cpu().numpy()
     h = 1e-3 * np.minimum(S_s[1], S_s[0] - S_s[1])
-    fd = _fd_gpu(Gs, dS[:, sep], dU[:, sep], dV[:, sep], h)
-    rel = np.sqrt(((fd - an) ** 2).sum(axis=0)) / np.sqrt((an ** 2).sum(axis=0))
+    rel = _rel(_fd_gpu(Gs, dS[:, sep], dU[:, sep], dV[:, sep], h), an)
     assert rel.max() < 1e-8, rel.max()
-    near = ratio > 1 - 2e-6
-    assert near.sum() > 200
+    # near-equal singular values
     Gn = np.ascontiguousarray(G[:, near])
     Un, Vn, Sn2 = _fwd(Gn)
     z = np.zeros((4, near.sum()))
     an = k2().gesvd2_bwd(Un, Sn2, Vn, t(dS[:, near])).cpu().numpy()
     S_n = Sn2.cpu().numpy()
     h = 1e-2 * (S_n[0] - S_n[1])
-    fd = _fd_gpu(Gn, dS[:, near], z, z, h)
-    rel = np.sqrt(((fd - an) ** 2).sum(axis=0)) / np.sqrt((an ** 2).sum(axis=0))
+    rel = _rel(_fd_gpu(Gn, dS[:, near], z, z, h), an)
     floor = 200 * EPS * S_n[0] / h
     assert np.all(rel <= 1e-8 + floor)
+    # widely separated: sigma1 alone with a step on its scale ...
+    Gw = np.ascontiguousarray(G[:, small])
+    Uw, Vw, Sw = _fwd(Gw)
+    S_w = Sw.cpu().numpy()
+    z = np.zeros((4, small.sum()))
+    dSa = np.zeros((2, small.sum()))
+    dSa[0] = dS[0, small]
+    an = k2().gesvd2_bwd(Uw, Sw, Vw, t(dSa)).cpu().numpy()
+    h = 1e-6 * S_w[0]
+    rel = _rel(_fd_gpu(Gw, dSa, z, z, h), an)
+    floor = 64 * EPS * S_w[0] / h
+    assert np.all(rel <= 1e-8 + floor), (rel / (1e-8 + floor)).max()
+    # ... and sigma2 alone with a step on its own scale
+    dSb = np.zeros_like(dSa)
+    dSb[1] = dS[1, small]
+    an = k2().gesvd2_bwd(Uw, Sw, Vw, t(dSb)).cpu().numpy()
+    h = 1e-3 * S_w[1]
+    rel = _rel(_fd_gpu(Gw, dSb, z, z, h, richardson=False), an)
+    floor = 64 * EPS * S_w[1] / h
+    assert np.all(rel <= 1e-8 + floor), (rel / (1e-8 + floor)).max()
 
 
 def test_autograd_function_gradcheck():
