@@ -189,7 +189,7 @@ SRC_GROUPS = {"2x2": SRC_2X2, "complex": SRC_2X2 + ("k2_complex.cu",), "bwd": ("
               "kog": SRC_2X2 + ("k2_kog.cu", "k2_kog_dev.cuh")}
 # The source hashes at which the count tables below were taken (profiles/pipe_ceilings.md).
 PIPE_COUNTS_HASH = {"2x2": "577b077599ba4a63", "complex": "0924564194c96378", "bwd": "f51322056ad56ee9",
-                    "kog": "e4d709a5eaa858fe"}
+                    "kog": "eebec41989091ded"}
 
 
 def _pc(group, unit, counts, dram):
@@ -216,9 +216,11 @@ PIPE_COUNTS = {
                                                       26.255, 1.3183, 0.083496), 634.61),
     "bwd_kernel<double>": _pc("bwd", "matrix", (16.355, 1.2188, 5.5112, 2.6453, 0.21848, 2.8638, 0.75116, 0.125,
                                                 1.0449, 0.034565, 0.12616), 188.63),
-    "kog_persistent<double>": _pc("kog", "rotation FP64 operation", (0.59587, 0.035221, 0.17541, 0.14531, 0.0040116,
-                                                                     0.14932, 0.055805, 0.0065938, 0.027849,
-                                                                     0.0027299, 0.012637), 0.0010445),
+    # the three instantiations of the 608-matrix run (orders <= 32 with U and V in shared
+    # memory, 33..64 with 64 registers, above 64) summed: one unit mix, a slightly lower bound
+    "kog_persistent<double>": _pc("kog", "rotation FP64 operation", (0.61330, 0.035216, 0.16611, 0.15956, 0.0040120,
+                                                                     0.16357, 0.061840, 0.0094780, 0.033440,
+                                                                     0.0041060, 0.0051660), 0.0010450),
 }
 
 
@@ -899,118 +901,82 @@ def host_bytes():
 
 
 def e2e_leg(steps, warmup, dev, D):
-    """End to end through the Python API on the headline batch: pinned host inputs ->
-    device -> kernels -> host outputs, in chunks over three streams with a buffer set each,
-    so that the host-to-device copy of one chunk, the kernels of another and the
-    device-to-host copy of a third run at the same time (ordering only within a stream; all
-    streams join at the end of a step).  Every copy and kernel of every chunk is bracketed
-    by CUDA events on its stream, so a slow step can be traced to the operation that was
-    slow."""
+    """End to end through the public API on the headline batch: the inputs (2^27 general and
+    2^27 triangular matrices) sit in pinned host memory, k2svd.svd2_host streams them through
+    the device in 2^22-matrix chunks (host-to-device copy, k2svd_dgesvd2 / k2svd_dtrsvd2,
+    device-to-host copy of U, V and S, on three streams), and a step ends when every output
+    is back in host memory."""
     import torch
     from paper_2407_13116_gb300 import inputs as I
     from paper_2407_13116_gb300 import k2svd
     torch.cuda.empty_cache()          # the earlier legs' cached blocks go back to the driver
     n, c = E2E_HALF, E2E_CHUNK
     # pinned host memory for inputs and outputs: 27 doubles per general + triangular pair
-    need = 2 * n * 27 * 8
-    if host_bytes() and need > 0.5 * host_bytes():
-        while n > c and 2 * n * 27 * 8 > 0.5 * host_bytes():
-            n //= 2
+    while n > c and host_bytes() and 2 * n * 27 * 8 > 0.5 * host_bytes():
+        n //= 2
     nc = n // c
     dt = torch.float64
-    NS = 3
     i0 = shard_offset(n, D.rank)
     Gh = torch.empty((nc, 4, c), dtype=dt, pin_memory=True)
     Th = torch.empty((nc, 3, c), dtype=dt, pin_memory=True)
     for q in range(nc):              # generated on the device chunk by chunk, kept in host memory
         Gh[q].copy_(I.general(c, SEED + 2, "d", "wide", i0=i0 + q * c, xp="torch", device=dev))
         Th[q].copy_(I.triangular(c, SEED + 3, "d", "wide", i0=i0 + q * c, xp="torch", device=dev))
-    outs = {k: torch.empty((nc, rows, c), dtype=dt, pin_memory=True) for k, rows in
-            (("Ug", 4), ("Vg", 4), ("Sg", 2), ("Ut", 4), ("Vt", 4), ("St", 2))}
-    streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
-    bufs = []
-    for _ in range(NS):
-        bufs.append({"G": torch.empty((4, c), dtype=dt, device=dev), "T": torch.empty((3, c), dtype=dt, device=dev),
-                     "U": torch.empty((4, c), dtype=dt, device=dev), "V": torch.empty((4, c), dtype=dt, device=dev),
-                     "S": torch.empty((2, c), dtype=dt, device=dev)})
-    main = torch.cuda.current_stream()
-    ops = 2 * nc
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(ops)]
-
-    def step(record):
-        for st in streams:
-            st.wait_stream(main)
-        j = 0
-        for kind in ("g", "t"):
-            for q in range(nc):
-                st, b = streams[j % NS], bufs[j % NS]
-                e = evs[j]
-                j += 1
-                with torch.cuda.stream(st):
-                    if record:
-                        e[0].record(st)
-                    if kind == "g":
-                        b["G"].copy_(Gh[q], non_blocking=True)
-                        if record:
-                            e[1].record(st)
-                        k2svd.gesvd2(b["G"], U=b["U"], V=b["V"], S=b["S"], want_info=False)
-                        U, V, S = outs["Ug"], outs["Vg"], outs["Sg"]
-                    else:
-                        b["T"].copy_(Th[q], non_blocking=True)
-                        if record:
-                            e[1].record(st)
-                        k2svd.trsvd2(b["T"][0], b["T"][1], b["T"][2], U=b["U"], V=b["V"], S=b["S"], want_info=False)
-                        U, V, S = outs["Ut"], outs["Vt"], outs["St"]
-                    if record:
-                        e[2].record(st)
-                    U[q].copy_(b["U"], non_blocking=True)
-                    V[q].copy_(b["V"], non_blocking=True)
-                    S[q].copy_(b["S"], non_blocking=True)
-                    if record:
-                        e[3].record(st)
-        for st in streams:
-            main.wait_stream(st)
-        torch.cuda.synchronize()
-
+    Og = torch.empty((nc, 10, c), dtype=dt, pin_memory=True)
+    Ot = torch.empty((nc, 10, c), dtype=dt, pin_memory=True)
+    jobs = [(Gh, Og, False), (Th, Ot, True)]
     for _ in range(warmup):
-        step(False)
+        k2svd.svd2_host(jobs, device=dev)
     D.barrier()
+    per = []
     t = time.perf_counter()
-    per, worst = [], {"h2d": 0.0, "kernel": 0.0, "d2h": 0.0}
-    sums = {"h2d": 0.0, "kernel": 0.0, "d2h": 0.0}
     for _ in range(steps):
         t1 = time.perf_counter()
-        step(True)
+        k2svd.svd2_host(jobs, device=dev)
         per.append(time.perf_counter() - t1)
-        for e in evs:
-            for nm, (a, b) in (("h2d", (0, 1)), ("kernel", (1, 2)), ("d2h", (2, 3))):
-                ms = e[a].elapsed_time(e[b])
-                worst[nm] = max(worst[nm], ms)
-                sums[nm] += ms
     el = D.max((time.perf_counter() - t) / steps)
+    # two more steps outside the timed region with every copy and kernel bracketed by events:
+    # where the time of a step goes (the device-to-host stream's busy time against the span)
+    traces = []
+    for _ in range(2):
+        tr = []
+        k2svd.svd2_host(jobs, device=dev, trace=tr)
+        traces.append(tr)
+    tr = max(traces, key=lambda x: x[-1]["end_ms"])
+    span = max(r["end_ms"] for r in tr)
+    trace_summary = {"span_ms": span, "d2h_busy_ms": sum(r["d2h_ms"] for r in tr),
+                     "h2d_busy_ms": sum(r["h2d_ms"] for r in tr), "kernel_busy_ms": sum(r["kernel_ms"] for r in tr),
+                     "max_d2h_ms": max(r["d2h_ms"] for r in tr), "max_h2d_ms": max(r["h2d_ms"] for r in tr),
+                     "max_kernel_ms": max(r["kernel_ms"] for r in tr)}
     h2d = (4 + 3) * 8 * n
     d2h = 2 * (4 + 4 + 2) * 8 * n
-    # the host link's own copy rates on this box (one pinned 1 GiB copy each way), for reading
-    # the end-to-end number: with these copies overlapped it is bound by the larger of
-    # h2d / h2d rate and d2h / d2h rate
+    # the host link's own copy rates on this box (one pinned 2 GiB copy each way, then both
+    # at once), for reading the end-to-end number
     link = {}
-    x = outs["Ug"].view(-1)[: 1 << 27]
+    x = Og.view(-1)[: 1 << 28]
     y = torch.empty(x.numel(), dtype=dt, device=dev)
-    for name, fn in (("h2d_gbs", lambda: y.copy_(x, non_blocking=True)), ("d2h_gbs", lambda: x.copy_(y, non_blocking=True))):
-        fn()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(); fn(); e1.record(); torch.cuda.synchronize()
-        link[name] = x.numel() * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9
-    del Gh, Th, outs, bufs, x, y
+    sa, sb = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def timed(ops):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for st, fn in ops:
+            with torch.cuda.stream(st):
+                fn()
+        torch.cuda.synchronize()
+        return x.numel() * 8 / (time.perf_counter() - t0) / 1e9
+    up, down = (sa, lambda: y.copy_(x, non_blocking=True)), (sb, lambda: x.copy_(y, non_blocking=True))
+    timed([up, down])
+    link["h2d_gbs"], link["d2h_gbs"], link["both_gbs_each"] = timed([up]), timed([down]), timed([up, down])
+    del Gh, Th, Og, Ot, x, y
     torch.cuda.empty_cache()
+    med = statistics.median(per)
     return {"value": D.world * 2 * n / el, "unit": "SVDs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "batch": 2 * n, "ms_per_step": el * 1e3, "streams": NS, "chunk": c, "link": link,
+            "batch": 2 * n, "ms_per_step": el * 1e3, "chunk": c, "api": "k2svd.svd2_host", "link": link,
             "copy_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6,
-            "step_ms_min_max": [min(per) * 1e3, max(per) * 1e3],
-            "step_ms_median": statistics.median(per) * 1e3,
-            "per_op_ms_mean": {k: v / (steps * ops) for k, v in sums.items()},
-            "per_op_ms_max": worst,
-            "note": "inputs and outputs in pinned host memory; the timed region holds every copy"}
+            "step_ms_min_max": [min(per) * 1e3, max(per) * 1e3], "step_ms_median": med * 1e3,
+            "mean_over_median": el / med, "traced_step": trace_summary,
+            "note": "inputs and outputs in pinned host memory; every copy is inside the timed region"}
 
 
 def cpu_baseline(seconds=10.0):
@@ -1089,6 +1055,8 @@ def run_ours(a):
            "config": headline_config(),
            "clocks": res["clocks"], "gpu_launches": res["launches"], "roofline": roofline,
            "pipe_rates": rates}
+    if D.world == 1 and not a.no_e2e:
+        out["e2e"] = e2e_leg(max(5, a.steps // 2), 1, dev, D)
     if not a.no_fp32:
         rs = leg("s", N_HALF_S, a.steps, a.warmup, dev, D, clocks_index=D.local)
         mss = D.max(rs["ms"])
@@ -1123,8 +1091,6 @@ def run_ours(a):
         out["kogbet_grad"] = kog_grad_leg(max(2, a.steps // 5), 1, dev, D)
     if not a.no_narrow:
         out["narrow"] = narrow_leg(a.steps, a.warmup, dev, D)
-    if D.world == 1 and not a.no_e2e:
-        out["e2e"] = e2e_leg(max(5, a.steps // 2), 1, dev, D)
     if D.rank == 0 and D.world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     D.close()

@@ -68,18 +68,30 @@ template <typename T> struct kog_params {
 __host__ __device__ constexpr int kog_piv_stride(int nmax) { return nmax / 2 + 1; }
 template <typename T> __host__ __device__ constexpr size_t kog_piv_elems(int nmax) { return (size_t)kog_piv_stride(nmax) * 10; }
 
+// Shared memory of the persistent kernel: G (unless in the workspace), two buffers of pivot
+// parameters, the column sums (nmax), perm and flip (2 nmax ints), then U and V (nmax^2 each)
+// when they are staged in shared memory too (uvs).
 template <typename T>
-__host__ __device__ inline size_t kog_smem_bytes(int nmax, bool gg)
+__host__ __device__ inline size_t kog_smem_bytes(int nmax, bool gg, bool uvs = false)
 {
     size_t g = gg ? 0 : (size_t)(nmax + 1) * nmax * sizeof(T);
-    return g + 2 * kog_piv_elems<T>(nmax) * sizeof(T) + (size_t)nmax * sizeof(T) + 2 * (size_t)nmax * sizeof(int) + 64;
+    size_t uv = uvs ? 2 * (size_t)nmax * nmax * sizeof(T) : 0;
+    return g + 2 * kog_piv_elems<T>(nmax) * sizeof(T) + (size_t)nmax * sizeof(T) + 2 * (size_t)nmax * sizeof(int) + uv +
+           64;
 }
+// U and V are staged in shared memory for orders up to KOG_UVS_MAX: the whole factorization
+// then runs in shared memory and they are written out once, permuted, at the end.  Measured
+// on the 8192-matrix workload (orders 8..128): the orders-8..32 bucket 9.35 ms against 9.68
+// with U and V in global memory; staging up to order 48 or 64 made those buckets slower
+// (33..64: 73.7 ms against 70.6 at 64), as the extra shared memory leaves fewer CTAs per SM
+// for steps that wait on their pivot SVDs.
+constexpr int KOG_UVS_MAX = 32;
 
 // ---------------------------------------------------------------------------------------
 // per-matrix phases shared by both forms (called by all threads of a block)
 // ---------------------------------------------------------------------------------------
 struct kog_sh {                       // block-shared scalars
-    int slot, kmax, bad;
+    int slot, kmax, bad, uv;
     double b;
 };
 
@@ -207,6 +219,50 @@ __device__ __forceinline__ void kog_rotate_uv(T *U, T *V, int n, int st, const T
     }
 }
 
+// The U and V updates of step st taken by whole warps from a shared work counter, 64 items
+// at a time (two per lane, loads first as in kog_rotate_uv): warps that finish their other
+// work early -- the pivot warps once their 2x2 SVDs are done -- take more of them.  Called by
+// converged warps; *ctr is zero at the start of the step.
+template <typename T>
+__device__ __forceinline__ void kog_rotate_uv_dyn(T *U, T *V, int n, int st, const T *piv, int ps, int *ctr)
+{
+    const int np = modulus_count(n, st);
+    const int items = np * n;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(ctr, 64);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= items) break;
+        const int wa = base + lane, wb = base + 32 + lane;
+        if (wb < items) {
+            const int r0 = wa % n, p0 = wa / n, r1 = wb % n, p1 = wb / n;
+            int i0, j0, i1, j1;
+            modulus_pair(n, st, p0, i0, j0);
+            modulus_pair(n, st, p1, i1, j1);
+            T *ua0 = U + (size_t)i0 * n + r0, *ub0 = U + (size_t)j0 * n + r0;
+            T *va0 = V + (size_t)i0 * n + r0, *vb0 = V + (size_t)j0 * n + r0;
+            T *ua1 = U + (size_t)i1 * n + r1, *ub1 = U + (size_t)j1 * n + r1;
+            T *va1 = V + (size_t)i1 * n + r1, *vb1 = V + (size_t)j1 * n + r1;
+            T x0 = *ua0, y0 = *ub0, s0 = *va0, t0v = *vb0, x1 = *ua1, y1 = *ub1, s1 = *va1, t1v = *vb1;
+            rot2(x0, y0, piv + p0, ps);
+            rot2(s0, t0v, piv + 4 * ps + p0, ps);
+            rot2(x1, y1, piv + p1, ps);
+            rot2(s1, t1v, piv + 4 * ps + p1, ps);
+            *ua0 = x0; *ub0 = y0; *va0 = s0; *vb0 = t0v;
+            *ua1 = x1; *ub1 = y1; *va1 = s1; *vb1 = t1v;
+        } else {
+            for (int w = wa; w < items; w += 32) {
+                const int r = w % n, p = w / n;
+                int i, j;
+                modulus_pair(n, st, p, i, j);
+                rot2(U[(size_t)i * n + r], U[(size_t)j * n + r], piv + p, ps);
+                rot2(V[(size_t)i * n + r], V[(size_t)j * n + r], piv + 4 * ps + p, ps);
+            }
+        }
+    }
+}
+
 // Element (r, c) of G_{k+1} computed from G_k and the rotations of step st, with the
 // operations phase 1 applies to it: the row rotation of r's pair (both columns of c's
 // group), then the column rotation of c's pair; sigma or zero inside a pivot block.
@@ -229,12 +285,14 @@ __device__ __forceinline__ T kog_next_entry(const T *G, int ld, int n, int st, c
 // One step st of the persistent form (parameters in pc), leaving the pivot parameters of
 // step nx in pn.  Ends with a block barrier.
 template <typename T>
-__device__ __forceinline__ void kog_step(T *G, int ld, T *U, T *V, int n, int st, int nx, const T *pc, T *pn, int ps)
+__device__ __forceinline__ void kog_step(T *G, int ld, T *U, T *V, int n, int st, int nx, const T *pc, T *pn, int ps,
+                                         int *uvc)
 {
     const int npn = modulus_count(n, nx);
     const int w0 = (npn + 31) & ~31;
     const int tid = threadIdx.x;
     if ((int)blockDim.x - w0 >= 32) {
+        if (tid == 0) *uvc = 0;
         T g11 = T(0), g21 = T(0), g12 = T(0), g22 = T(0);
         if (tid < npn) {
             int i, j;
@@ -247,10 +305,11 @@ __device__ __forceinline__ void kog_step(T *G, int ld, T *U, T *V, int n, int st
         __syncthreads();                                    // G_k read before phase 1 writes
         if (tid < w0) {
             if (tid < npn) kog_pivot(g11, g21, g12, g22, pn + tid, ps);
+            __syncwarp();
         } else {
             kog_rotate_g(G, ld, n, st, pc, ps, tid - w0, blockDim.x - w0);
-            kog_rotate_uv(U, V, n, st, pc, ps, tid - w0, blockDim.x - w0);
         }
+        kog_rotate_uv_dyn(U, V, n, st, pc, ps, uvc);     // every warp, the pivot warps too
     } else {
         kog_rotate_g(G, ld, n, st, pc, ps, tid, blockDim.x);
         __syncthreads();
@@ -261,9 +320,11 @@ __device__ __forceinline__ void kog_step(T *G, int ld, T *U, T *V, int n, int st
 }
 
 // Sort the diagonal (descending, stable), write S, permute the columns of U and V through
-// the staging area `stage` (n*n elements, may be G).
+// the staging area `stage` (n*n elements, may be G), or, when U and V were staged in shared
+// memory (Us, Vs), straight from there into U and V.
 template <typename T>
-__device__ void kog_finish(const T *G, int ld, T *U, T *V, T *S, int n, int k, T *dg, int *perm, T *stage)
+__device__ void kog_finish(const T *G, int ld, T *U, T *V, T *S, int n, int k, T *dg, int *perm, T *stage,
+                           const T *Us = nullptr, const T *Vs = nullptr)
 {
     // a negative diagonal element gives its sign to U's column (stored in the sign of dg's
     // slot as a flag array after the sort); |g_qq| are ranked
@@ -288,11 +349,15 @@ __device__ void kog_finish(const T *G, int ld, T *U, T *V, T *S, int n, int k, T
     const int nn = n * n;
     for (int pass = 0; pass < 2; ++pass) {
         T *X = pass ? V : U;
-        for (int e = threadIdx.x; e < nn; e += blockDim.x) stage[e] = X[e];
-        __syncthreads();
+        const T *from = pass ? Vs : Us;
+        if (!from) {
+            for (int e = threadIdx.x; e < nn; e += blockDim.x) stage[e] = X[e];
+            __syncthreads();
+            from = stage;
+        }
         for (int e = threadIdx.x; e < nn; e += blockDim.x) {
             const int src = perm[e / n];
-            const T x = stage[(size_t)src * n + e % n];
+            const T x = from[(size_t)src * n + e % n];
             X[e] = (pass == 0 && flip[src]) ? -x : x;
         }
         __syncthreads();
@@ -310,8 +375,12 @@ __device__ void kog_fail(T *U, T *V, T *S, int n)
 // ---------------------------------------------------------------------------------------
 // persistent kernel
 // ---------------------------------------------------------------------------------------
-template <typename T, bool GG>
-__global__ void __launch_bounds__(512) kog_persistent(const kog_params<T> P)
+// MINB = 2 caps the registers at 64 a thread so that more CTAs share an SM: for buckets up
+// to order 64, whose steps are bound by the latency of their pivot SVDs rather than by the
+// FP64 rotations (order 64: 0.72 of the rotation floor against 0.65; order 128 and the
+// whole 8192-matrix workload were slower with the cap).
+template <typename T, bool GG, int MINB, bool UVS, int MAXT = 512>
+__global__ void __launch_bounds__(MAXT, MINB) kog_persistent(const kog_params<T> P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ kog_sh sh;
@@ -320,6 +389,8 @@ __global__ void __launch_bounds__(512) kog_persistent(const kog_params<T> P)
     const int ps = kog_piv_stride(P.nmax);
     T *colsum = piv + 2 * kog_piv_elems<T>(P.nmax);
     int *perm = reinterpret_cast<int *>(colsum + P.nmax);
+    T *Us = UVS ? reinterpret_cast<T *>(perm + 2 * P.nmax) : nullptr;
+    T *Vs = UVS ? Us + (size_t)P.nmax * P.nmax : nullptr;
     for (;;) {
         if (threadIdx.x == 0) sh.slot = atomicAdd(P.queue, 1);
         __syncthreads();
@@ -330,7 +401,8 @@ __global__ void __launch_bounds__(512) kog_persistent(const kog_params<T> P)
         const int n = d.n, ld = GG ? n : n + 1;
         T *G = GG ? P.gws + d.goff : Gs;
         T *U = P.U + d.off, *V = P.V + d.off, *S = P.S + d.soff;
-        const int k = kog_load(P.A + d.off, G, ld, U, V, n, &sh);
+        T *Uw = UVS ? Us : U, *Vw = UVS ? Vs : V;        // where the sweeps update U and V
+        const int k = kog_load(P.A + d.off, G, ld, Uw, Vw, n, &sh);
         if (k == INT_MIN) {
             kog_fail(U, V, S, n);
             if (threadIdx.x == 0) {
@@ -355,14 +427,14 @@ __global__ void __launch_bounds__(512) kog_persistent(const kog_params<T> P)
             for (int st = 0; st < n; ++st) {
                 // the pivots of the next step: step 0 of the next sweep after the last one
                 // (unused when the sweeps end)
-                kog_step(G, ld, U, V, n, st, st + 1 < n ? st + 1 : 0, pc, pn, ps);
+                kog_step(G, ld, Uw, Vw, n, st, st + 1 < n ? st + 1 : 0, pc, pn, ps, &sh.uv);
                 T *t = pc; pc = pn; pn = t;
             }
             ++sw;
             off = kog_norm(G, n, ld, true, colsum, bc);
             go = !(off < tol) && sw < P.max_sweeps && off > T(0);
         }
-        kog_finish(G, ld, U, V, S, n, k, colsum, perm, G);
+        kog_finish(G, ld, U, V, S, n, k, colsum, perm, G, Us, Vs);
         if (threadIdx.x == 0) {
             if (P.sweeps) P.sweeps[d.idx] = sw;
             if (P.info) P.info[d.idx] = (off < tol || off == T(0)) ? 0 : 1;
@@ -902,8 +974,11 @@ template <typename T, bool GG, bool DYN>
 static cudaError_t launch_bucket_k(const kog_params<T> &Pin, int threads, cudaStream_t st, int *queue_dev)
 {
     kog_params<T> P = Pin;
-    auto kern = DYN ? kog_dynamic<T, GG> : kog_persistent<T, GG>;
-    size_t smem = kog_smem_bytes<T>(P.nmax, GG);
+    const bool uvs = !GG && !DYN && P.nmax <= KOG_UVS_MAX;
+    auto kern = DYN ? kog_dynamic<T, GG>
+                    : (P.nmax <= 64 ? (uvs ? kog_persistent<T, GG, 2, true> : kog_persistent<T, GG, 2, false>)
+                       : threads > 512 ? kog_persistent<T, GG, 1, false, 1024> : kog_persistent<T, GG, 1, false>);
+    size_t smem = kog_smem_bytes<T>(P.nmax, GG, uvs);
     P.wsm = 0;
     if (DYN) {                                         // the weights in shared memory when they fit
         int dev = 0, optin = 0;
@@ -973,7 +1048,7 @@ static int autotune(const kog_plan<T> &pl, const kog_params<T> &base, cudaStream
             if (it != g_tuned.end()) { threads[b] = it->second; continue; }
         }
         if (!tune) continue;
-        const int cand[5] = {32, 64, 128, 256, 512};
+        const int cand[6] = {32, 64, 128, 256, 512, 1024};
         kog_params<T> P = base;
         P.desc = reinterpret_cast<const kog_desc *>(ws + pl.off_desc) + pl.bstart[b];
         P.count = std::min(cnt, 4 * sms);
@@ -984,7 +1059,7 @@ static int autotune(const kog_plan<T> &pl, const kog_params<T> &base, cudaStream
         float best = 1e30f;
         int bestt = threads[b];
         for (int t : cand) {
-            if (t < 32) continue;
+            if (t > 512 && (pl.dyn || P.nmax <= 64)) continue;   // 1024 threads: the 64-register kernel of orders > 64
             cudaEventRecord(e0, st);
             cudaError_t e = launch_bucket<T>(P, b, pl.dyn, t, st, P.queue);
             cudaEventRecord(e1, st);
