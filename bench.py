@@ -1056,7 +1056,7 @@ def run_ours(a):
            "clocks": res["clocks"], "gpu_launches": res["launches"], "roofline": roofline,
            "pipe_rates": rates}
     if D.world == 1 and not a.no_e2e:
-        out["e2e"] = e2e_leg(max(5, a.steps // 2), 1, dev, D)
+        out["e2e"] = e2e_leg(max(8, a.steps), 1, dev, D)
     if not a.no_fp32:
         rs = leg("s", N_HALF_S, a.steps, a.warmup, dev, D, clocks_index=D.local)
         mss = D.max(rs["ms"])

@@ -156,6 +156,21 @@ template <typename T> struct tri_out {
     ef<T> s1, s2;
 };
 
+// Alg. 1's test fl(x / y) < eps (eps = 2^-p) for x, y > 0 given as (e,f) pairs, decided exactly
+// without the division.  With d = e_x - e_y and f_x, f_y in [1, 2) on the grid 2^-(p-1), the
+// quotient is q = (f_x / f_y) 2^d with f_x / f_y in (1/2, 2), and fl(q) < 2^-p exactly when q
+// lies below the midpoint 2^-p (1 - 2^-(p+1)) between 2^-p and its predecessor (at the midpoint
+// the tie goes to the even 2^-p):
+//   * d < -p: q <= (2 - 2^-(p-1)) 2^-(p+1) = 2^-p (1 - 2^-p), below the midpoint;
+//   * d > -p: q > 2^-p;
+//   * d = -p: q >= 2^-p when f_x >= f_y; when f_x < f_y, f_x <= f_y - 2^-(p-1), so
+//     f_x / f_y < 1 - 2^-p, below the midpoint.
+template <typename T> __device__ __forceinline__ bool quot_below_eps(ef<T> x, ef<T> y)
+{
+    const int d = x.e - y.e;
+    return d < -fpt<T>::P || (d == -fpt<T>::P && pos_lt(x.f, y.f));
+}
+
 // The cos/sin divisions of the triangular SVD: on the FP64 divider when FDIV (the caller's
 // FP64 pipe has room: general matrices), else as every other division.  Same results.
 template <bool FDIV, typename T> __device__ __forceinline__ T csdiv(T a, T b) { return FDIV ? a / b : qdiv(a, b); }
@@ -184,7 +199,7 @@ __device__ __forceinline__ void tri_svd(T r11, T r12, T r22, tri_out<T> &z, int 
     } else if (pos_eq(rb, rc)) {                                 // eq. (t2f''')
         kind = 1; Y = ef_mul(era, era);
         flags |= FL_T2F3;
-    } else if (pos_lt(qdiv(ra, rb), fpt<T>::eps())) {                 // eq. (t2f''), only for t' ~ 13
+    } else if (quot_below_eps(era, erb)) {                       // eq. (t2f''), only for t' ~ 13
         kind = 0;
         flags |= FL_T2F2;
     } else if (!NCR) {                                     // eq. (t2f')
