@@ -188,7 +188,7 @@ SRC_2X2 = ("k2_fp.cuh", "k2_svd2.cuh", "k2_svd2_kernel.cuh", "k2_gesvd2.cu")
 SRC_GROUPS = {"2x2": SRC_2X2, "complex": SRC_2X2 + ("k2_complex.cu",), "bwd": ("k2_fp.cuh", "k2_bwd.cu"),
               "kog": SRC_2X2 + ("k2_kog.cu", "k2_kog_dev.cuh")}
 # The source hashes at which the count tables below were taken (profiles/pipe_ceilings.md).
-PIPE_COUNTS_HASH = {"2x2": "577b077599ba4a63", "complex": "0924564194c96378", "bwd": "f51322056ad56ee9",
+PIPE_COUNTS_HASH = {"2x2": "94132a1fb5b917d9", "complex": "2cc138c4b355db87", "bwd": "f51322056ad56ee9",
                     "kog": "eebec41989091ded"}
 
 
@@ -200,22 +200,14 @@ def _pc(group, unit, counts, dram):
 # kernel -> (source group, unit, {pipe: warp instructions per unit}, DRAM bytes per unit under
 # ncu, caches flushed before each launch); 2^22-matrix captures of the benchmark workloads
 PIPE_COUNTS = {
-    "svd2a_kernel<double>": _pc("2x2", "matrix", (80.612, 1.3574, 43.827, 15.156, 1.5589, 16.715, 2.4225, 1.1828,
-                                                  6.5166, 0.26554, 0.0023193), 113.22),
-    "svd2b_kernel<double>": _pc("2x2", "matrix", (121.92, 1.3503, 56.488, 28.429, 2.9762, 31.406, 9.0118, 1.9121,
-                                                  11.736, 0.63089, 0.12732), 135.11),
-    "svd2_kernel<double,tri>": _pc("2x2", "matrix", (105.94, 1.4394, 49.661, 26.934, 2.4759, 29.41, 2.9868, 1.6091,
-                                                     11.059, 0.46691, 0.12732), 102.5),
-    "svd2_kernel<float,general>": _pc("2x2", "matrix", (85.492, 0.53125, 36.175, 18.157, 7.3987, 25.555, 1.6011,
-                                                        2.2688, 9.3348, 0.59087, 0.12732), 46.698),
-    "svd2_kernel<float,tri>": _pc("2x2", "matrix", (53.349, 0.0, 23.397, 10.942, 4.765, 15.707, 0.93654, 1.2987,
-                                                    6.432, 0.31998, 0.12732), 39.785),
-    "lasv2_kernel<double>": _pc("2x2", "matrix", (103.35, 1.4707, 49.69, 24.939, 2.4763, 27.416, 2.4509, 1.6091,
-                                                  11.184, 0.46695, 0.0023193), 72.12),
-    "csvd2_kernel<double>": _pc("complex", "matrix", (270.06, 4.2253, 119.46, 69.961, 6.1946, 76.155, 11.048, 4.0908,
-                                                      26.255, 1.3183, 0.083496), 634.61),
-    "bwd_kernel<double>": _pc("bwd", "matrix", (16.355, 1.2188, 5.5112, 2.6453, 0.21848, 2.8638, 0.75116, 0.125,
-                                                1.0449, 0.034565, 0.12616), 188.63),
+    "svd2a_kernel<double>": _pc("2x2", "matrix", (80.612, 1.3574, 43.827, 15.156, 1.5593, 16.715, 2.4225, 1.1828, 6.5166, 0.26546, 0.0023193), 113.07),
+    "svd2b_kernel<double>": _pc("2x2", "matrix", (116.39, 1.3503, 54.034, 27.184, 2.758, 29.942, 8.5144, 1.7869, 11.121, 0.60196, 0.125), 135.47),
+    "svd2_kernel<double,tri>": _pc("2x2", "matrix", (100.61, 1.4394, 47.036, 25.428, 2.2596, 27.688, 3.1595, 1.4839, 10.404, 0.43571, 0.12732), 100.6),
+    "svd2_kernel<float,general>": _pc("2x2", "matrix", (83.694, 0.53125, 35.634, 18.225, 7.0244, 25.249, 1.2257, 2.1746, 9.0441, 0.55959, 0.12732), 46.056),
+    "svd2_kernel<float,tri>": _pc("2x2", "matrix", (50.633, 0, 22.662, 10.339, 4.3216, 14.661, 0.69446, 1.2046, 6.087, 0.2888, 0.12732), 39.136),
+    "lasv2_kernel<double>": _pc("2x2", "matrix", (98.237, 1.4707, 47.182, 23.393, 2.2597, 25.653, 2.7323, 1.4839, 10.529, 0.43576, 0.0023193), 74.032),
+    "csvd2_kernel<double>": _pc("complex", "matrix", (265.53, 4.2253, 116.98, 68.339, 6.1931, 74.533, 11.673, 3.9658, 25.641, 1.287, 0.085815), 654.15),
+    "bwd_kernel<double>": _pc("bwd", "matrix", (16.355, 1.2188, 5.5112, 2.6453, 0.21848, 2.8638, 0.75116, 0.125, 1.0449, 0.034637, 0.12616), 188.63),
     # the three instantiations of the 608-matrix run (orders <= 32 with U and V in shared
     # memory, 33..64 with 64 registers, above 64) summed: one unit mix, a slightly lower bound
     "kog_persistent<double>": _pc("kog", "rotation FP64 operation", (0.61330, 0.035216, 0.16611, 0.15956, 0.0040120,

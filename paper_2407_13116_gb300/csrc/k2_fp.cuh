@@ -227,6 +227,11 @@ __device__ __forceinline__ double div_rn_body(double a, double b)
 static __device__ __noinline__ uint64_t div_rn_bits(uint64_t a, uint64_t b) { return dbits(div_rn_body(dfrom(a), dfrom(b))); }
 __device__ __forceinline__ double div_rn(double a, double b) { return dfrom(div_rn_bits(dbits(a), dbits(b))); }
 
+// The FP64 divider's correctly rounded quotient, out of line: one copy of the division
+// sequence however many call sites use it (bit patterns in and out, as div_rn).
+static __device__ __noinline__ uint64_t fdiv_rn_bits(uint64_t a, uint64_t b) { return dbits(__ddiv_rn(dfrom(a), dfrom(b))); }
+__device__ __forceinline__ double fdiv_rn(double a, double b) { return dfrom(fdiv_rn_bits(dbits(a), dbits(b))); }
+
 // the method's divisions: binary64 on the integer pipes, binary32 on the FP32 pipe
 __device__ __forceinline__ double qdiv(double a, double b) { return div_rn(a, b); }
 __device__ __forceinline__ float qdiv(float a, float b) { return a / b; }

@@ -146,39 +146,43 @@ __device__ __forceinline__ void kog_pivots(const T *G, int ld, int n, int st, T 
 // group a and the columns of group b, a group being a pivot pair (a < np) or an unpaired
 // index.  Each element gets the row rotation first, then the column rotation.
 template <typename T>
+__device__ __forceinline__ void kog_g_item(T *G, int ld, int n, int st, int np, int nq, const T *piv, int ps, int w)
+{
+    const int a = w % nq, b = w / nq;
+    int ia, ja = -1, ib, jb = -1;
+    if (a < np) modulus_pair(n, st, a, ia, ja); else ia = modulus_single(n, st, a - np);
+    if (b < np) modulus_pair(n, st, b, ib, jb); else ib = modulus_single(n, st, b - np);
+    if (ja < 0 && jb < 0) return;                              // unpaired row and column
+    if (a == b) {                                              // the pivot block -> diag(sigma)
+        G[(size_t)ia * ld + ia] = piv[8 * ps + a];
+        G[(size_t)ia * ld + ja] = T(0);
+        G[(size_t)ja * ld + ia] = T(0);
+        G[(size_t)ja * ld + ja] = piv[9 * ps + a];
+        return;
+    }
+    T *c0 = G + (size_t)ib * ld, *c1 = jb >= 0 ? G + (size_t)jb * ld : nullptr;
+    T x00 = c0[ia], x10 = T(0), x01 = T(0), x11 = T(0);
+    if (ja >= 0) x10 = c0[ja];
+    if (jb >= 0) { x01 = c1[ia]; if (ja >= 0) x11 = c1[ja]; }
+    if (ja >= 0) {                                             // rows ia, ja <- U-hat^T
+        rot2(x00, x10, piv + a, ps);
+        if (jb >= 0) rot2(x01, x11, piv + a, ps);
+    }
+    if (jb >= 0) {                                             // columns ib, jb <- V-hat
+        rot2(x00, x01, piv + 4 * ps + b, ps);
+        if (ja >= 0) rot2(x10, x11, piv + 4 * ps + b, ps);
+    }
+    c0[ia] = x00;
+    if (ja >= 0) c0[ja] = x10;
+    if (jb >= 0) { c1[ia] = x01; if (ja >= 0) c1[ja] = x11; }
+}
+
+template <typename T>
 __device__ __forceinline__ void kog_rotate_g(T *G, int ld, int n, int st, const T *piv, int ps, int t0, int tn)
 {
     const int np = modulus_count(n, st), nq = n - np;          // groups: np pairs + (n - 2 np) singles
     const int items = nq * nq;
-    for (int w = t0; w < items; w += tn) {
-        const int a = w % nq, b = w / nq;
-        int ia, ja = -1, ib, jb = -1;
-        if (a < np) modulus_pair(n, st, a, ia, ja); else ia = modulus_single(n, st, a - np);
-        if (b < np) modulus_pair(n, st, b, ib, jb); else ib = modulus_single(n, st, b - np);
-        if (ja < 0 && jb < 0) continue;                        // unpaired row and column
-        if (a == b) {                                // the pivot block -> diag(sigma)
-            G[(size_t)ia * ld + ia] = piv[8 * ps + a];
-            G[(size_t)ia * ld + ja] = T(0);
-            G[(size_t)ja * ld + ia] = T(0);
-            G[(size_t)ja * ld + ja] = piv[9 * ps + a];
-            continue;
-        }
-        T *c0 = G + (size_t)ib * ld, *c1 = jb >= 0 ? G + (size_t)jb * ld : nullptr;
-        T x00 = c0[ia], x10 = T(0), x01 = T(0), x11 = T(0);
-        if (ja >= 0) x10 = c0[ja];
-        if (jb >= 0) { x01 = c1[ia]; if (ja >= 0) x11 = c1[ja]; }
-        if (ja >= 0) {                                         // rows ia, ja <- U-hat^T
-            rot2(x00, x10, piv + a, ps);
-            if (jb >= 0) rot2(x01, x11, piv + a, ps);
-        }
-        if (jb >= 0) {                                         // columns ib, jb <- V-hat
-            rot2(x00, x01, piv + 4 * ps + b, ps);
-            if (ja >= 0) rot2(x10, x11, piv + 4 * ps + b, ps);
-        }
-        c0[ia] = x00;
-        if (ja >= 0) c0[ja] = x10;
-        if (jb >= 0) { c1[ia] = x01; if (ja >= 0) c1[ja] = x11; }
-    }
+    for (int w = t0; w < items; w += tn) kog_g_item(G, ld, n, st, np, nq, piv, ps, w);
 }
 
 // U and V updates of step st (columns i, j of U <- U-hat, of V <- V-hat) by threads
