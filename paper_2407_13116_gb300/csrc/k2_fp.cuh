@@ -235,6 +235,10 @@ __device__ __forceinline__ double fdiv_rn(double a, double b) { return dfrom(fdi
 // the method's divisions: binary64 on the integer pipes, binary32 on the FP32 pipe
 __device__ __forceinline__ double qdiv(double a, double b) { return div_rn(a, b); }
 __device__ __forceinline__ float qdiv(float a, float b) { return a / b; }
+// the same quotient with the binary64 body inlined at the call site, for a division that is
+// the only one of its kernel half (no call, no shared body to fetch)
+__device__ __forceinline__ double qdiv_inl(double a, double b) { return div_rn_body(a, b); }
+__device__ __forceinline__ float qdiv_inl(float a, float b) { return a / b; }
 
 // ---------------------------------------------------------------------------------------
 // Exponent-"mantissa" pairs (Sect. 2): w = f 2^e with 1 <= |f| < 2, or (0, 0).
