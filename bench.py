@@ -188,8 +188,8 @@ SRC_2X2 = ("k2_fp.cuh", "k2_svd2.cuh", "k2_svd2_kernel.cuh", "k2_gesvd2.cu")
 SRC_GROUPS = {"2x2": SRC_2X2, "complex": SRC_2X2 + ("k2_complex.cu",), "bwd": ("k2_fp.cuh", "k2_bwd.cu"),
               "kog": SRC_2X2 + ("k2_kog.cu", "k2_kog_dev.cuh")}
 # The source hashes at which the count tables below were taken (profiles/pipe_ceilings.md).
-PIPE_COUNTS_HASH = {"2x2": "922543907621d8d0", "complex": "97f9dcb4bfa32f87", "bwd": "5d4a8a4a66914bf7",
-                    "kog": "f7e52321c658e592"}
+PIPE_COUNTS_HASH = {"2x2": "66c5311866092db6", "complex": "863ca888f717e75a", "bwd": "411a7ed9f6c0a0b6",
+                    "kog": "9a22e2cec6e4d228"}
 
 
 def _pc(group, unit, counts, dram):
@@ -200,19 +200,19 @@ def _pc(group, unit, counts, dram):
 # kernel -> (source group, unit, {pipe: warp instructions per unit}, DRAM bytes per unit under
 # ncu, caches flushed before each launch); 2^22-matrix captures of the benchmark workloads
 PIPE_COUNTS = {
-    "svd2a_kernel<double>": _pc("2x2", "matrix", (81.583, 1.2949, 43.89, 16.038, 1.5231, 17.561, 2.4537, 1.1828, 6.6512, 0.33755, 0.0023193), 108.58),
-    "svd2b_kernel<double>": _pc("2x2", "matrix", (116.39, 1.3503, 54.034, 27.184, 2.7579, 29.942, 8.5144, 1.7869, 11.121, 0.60193, 0.125), 135.49),
-    "svd2_kernel<double,tri>": _pc("2x2", "matrix", (100.61, 1.4394, 47.036, 25.429, 2.2596, 27.688, 3.1595, 1.4839, 10.404, 0.43561, 0.12732), 100.65),
-    "svd2_kernel<float,general>": _pc("2x2", "matrix", (83.694, 0.53125, 35.634, 18.224, 7.0255, 25.249, 1.2257, 2.1746, 9.0441, 0.55965, 0.12732), 46.009),
-    "svd2_kernel<float,tri>": _pc("2x2", "matrix", (50.633, 0, 22.662, 10.339, 4.3219, 14.661, 0.69446, 1.2046, 6.087, 0.28867, 0.12732), 39.14),
-    "lasv2_kernel<double>": _pc("2x2", "matrix", (98.237, 1.4707, 47.182, 23.393, 2.2597, 25.653, 2.7323, 1.4839, 10.529, 0.43566, 0.0023193), 74.037),
-    "csvd2_kernel<double>": _pc("complex", "matrix", (265.53, 4.2253, 116.98, 68.34, 6.193, 74.533, 11.673, 3.9658, 25.641, 1.2871, 0.085815), 654.64),
-    "bwd_kernel<double>": _pc("bwd", "matrix", (16.355, 1.2188, 5.5112, 2.6453, 0.21848, 2.8638, 0.75116, 0.125, 1.0449, 0.034616, 0.12616), 188.63),
+    "svd2a_kernel<double>": _pc("2x2", "matrix", (81.284, 1.3574, 43.682, 15.843, 1.5647, 17.407, 2.4248, 1.1828, 6.5887, 0.30869, 0), 101.4),
+    "svd2b_kernel<double>": _pc("2x2", "matrix", (116.39, 1.3503, 54.034, 27.184, 2.7579, 29.942, 8.5144, 1.7869, 11.121, 0.60196, 0.125), 135.55),
+    "svd2_kernel<double,tri>": _pc("2x2", "matrix", (100.61, 1.4394, 47.036, 25.429, 2.2595, 27.688, 3.1595, 1.4839, 10.404, 0.43565, 0.12732), 100.64),
+    "svd2_kernel<float,general>": _pc("2x2", "matrix", (83.694, 0.53125, 35.634, 18.224, 7.0246, 25.249, 1.2257, 2.1746, 9.0441, 0.55958, 0.12732), 46.024),
+    "svd2_kernel<float,tri>": _pc("2x2", "matrix", (50.633, 0, 22.662, 10.339, 4.3216, 14.661, 0.69446, 1.2046, 6.087, 0.2887, 0.12732), 39.138),
+    "lasv2_kernel<double>": _pc("2x2", "matrix", (98.237, 1.4707, 47.182, 23.393, 2.2597, 25.653, 2.7323, 1.4839, 10.529, 0.43565, 0.0023193), 74.048),
+    "csvd2_kernel<double>": _pc("complex", "matrix", (265.53, 4.2253, 116.98, 68.34, 6.1931, 74.533, 11.673, 3.9658, 25.641, 1.2871, 0.085815), 654.65),
+    "bwd_kernel<double>": _pc("bwd", "matrix", (16.355, 1.2188, 5.5112, 2.6453, 0.21848, 2.8638, 0.75116, 0.125, 1.0449, 0.034611, 0.12616), 188.62),
     # the three instantiations of the 608-matrix run (orders <= 32 with U and V in shared
     # memory, 33..64 with 64 registers, above 64) summed: one unit mix, a slightly lower bound
     "kog_persistent<double>": _pc("kog", "rotation FP64 operation", (0.60907, 0.035216, 0.16407, 0.15840, 0.0038365,
                                                                      0.16223, 0.061835, 0.0093784, 0.032952,
-                                                                     0.0040808, 0.0051653), 0.0010545),
+                                                                     0.0040808, 0.0051653), 0.0010348),
 }
 
 

@@ -87,3 +87,47 @@ def test_torch_helpers_roundtrip():
     Uc, Vc = k2().planes_to_complex(U), k2().planes_to_complex(V)
     R = Uc @ torch.diag_embed(S.T.to(torch.complex128)) @ Vc.conj().transpose(-1, -2)
     assert torch.allclose(R, A, atol=1e-14 * A.abs().max().item())
+
+
+def test_large_batch_all_patterns_strided():
+    """One batch of more than 65536 double matrices: every zero pattern, real, purely
+    imaginary and non-finite input, on strided planes, checked against the oracle bit for
+    bit, and nothing written past the batch."""
+    T = np.float64
+    rng = np.random.default_rng(77)
+    parts = []
+    for pattern in (None, 15, 7, 11, 13, 14, 3, 12, 5, 10, 9, 6, 1, 8):
+        parts.append(_planes(_random(4000, rng, -300, 300, T, pattern) + _random(1001, rng, -8, 8, T, pattern), T))
+    Gr = I.general(3001, 35, "d", "wide")
+    n = Gr.shape[1]
+    G = np.zeros((8, 2 * n + 3), T)
+    G[0::2, :n] = Gr
+    G[1::2, n:2 * n] = Gr
+    G[:, -3] = 1.0
+    G[5, -3] = np.inf
+    G[2, -1] = np.nan
+    parts.append(G)
+    G = np.ascontiguousarray(np.concatenate(parts, axis=1))
+    m = G.shape[1]
+    assert m >= (1 << 16)
+    ld = m + 5
+    Gt = torch.zeros((8, ld), dtype=torch.float64, device=DEV)
+    Gt[:, :m] = torch.from_numpy(G).to(DEV)
+    U = torch.full((8, ld), 7.0, dtype=torch.float64, device=DEV)
+    V = torch.full((8, ld), 7.0, dtype=torch.float64, device=DEV)
+    S = torch.full((2, ld), 7.0, dtype=torch.float64, device=DEV)
+    info = torch.full((ld,), 7, dtype=torch.int32, device=DEV)
+    import ctypes as C
+    p = lambda t: C.c_void_p(t.data_ptr())
+    rc = k2().lib().k2svd_zgesvd2(m, p(Gt), ld, p(U), ld, p(V), ld, p(S), ld, p(info),
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    rU, rV, rS, rinfo = oracle.cgesvd2(G, "d", nthreads=8)
+    for g, r, nm in ((U[:, :m], rU, "U"), (V[:, :m], rV, "V"), (S[:, :m], rS, "S")):
+        g = g.cpu().numpy()
+        nan = np.isnan(g) & np.isnan(r)
+        bad = (_bits(g) != _bits(r)) & ~nan
+        assert not bad.any(), (nm, np.argwhere(bad)[:4].tolist())
+    assert np.array_equal(info[:m].cpu().numpy(), rinfo)
+    assert (U[:, m:] == 7.0).all() and (V[:, m:] == 7.0).all() and (S[:, m:] == 7.0).all() and (info[m:] == 7).all()
