@@ -967,6 +967,7 @@ def e2e_leg(steps, warmup, dev, D):
             "batch": 2 * n, "ms_per_step": el * 1e3, "chunk": c, "api": "k2svd.svd2_host", "link": link,
             "copy_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6,
             "step_ms_min_max": [min(per) * 1e3, max(per) * 1e3], "step_ms_median": med * 1e3,
+            "step_ms": [round(x * 1e3, 2) for x in per],
             "mean_over_median": el / med, "traced_step": trace_summary,
             "note": "inputs and outputs in pinned host memory; every copy is inside the timed region"}
 
