@@ -975,7 +975,7 @@ static std::map<tune_key, int> g_tuned;
 static int default_threads(int nmax) { return nmax <= 32 ? 64 : (nmax <= 64 ? 256 : 512); }
 
 template <typename T, bool GG, bool DYN>
-static cudaError_t launch_bucket_k(const kog_params<T> &Pin, int threads, cudaStream_t st, int *queue_dev)
+static cudaError_t launch_bucket_k(const kog_params<T> &Pin, int threads, cudaStream_t st, int *queue_dev, int prio)
 {
     kog_params<T> P = Pin;
     const bool uvs = !GG && !DYN && P.nmax <= KOG_UVS_MAX;
@@ -1000,24 +1000,88 @@ static cudaError_t launch_bucket_k(const kog_params<T> &Pin, int threads, cudaSt
     if (blocks < 1) return cudaSuccess;
     e = cudaMemsetAsync(queue_dev, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    kern<<<blocks, threads, smem, st>>>(P);
-    return cudaPeekAtLastError();
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = prio;
+    cfg.attrs = attr;
+    cfg.numAttrs = prio != 0 ? 1 : 0;                 // else the stream's own priority
+    return cudaLaunchKernelEx(&cfg, kern, P);
 }
 
 template <typename T>
-static cudaError_t launch_bucket(const kog_params<T> &P, int bucket, bool dyn, int threads, cudaStream_t st, int *queue_dev)
+static cudaError_t launch_bucket(const kog_params<T> &P, int bucket, bool dyn, int threads, cudaStream_t st, int *queue_dev,
+                                 int prio = 0)
 {
     if (bucket == BUCKET_GLOBAL)
-        return dyn ? launch_bucket_k<T, true, true>(P, threads, st, queue_dev) : launch_bucket_k<T, true, false>(P, threads, st, queue_dev);
-    return dyn ? launch_bucket_k<T, false, true>(P, threads, st, queue_dev) : launch_bucket_k<T, false, false>(P, threads, st, queue_dev);
+        return dyn ? launch_bucket_k<T, true, true>(P, threads, st, queue_dev, prio) : launch_bucket_k<T, true, false>(P, threads, st, queue_dev, prio);
+    return dyn ? launch_bucket_k<T, false, true>(P, threads, st, queue_dev, prio) : launch_bucket_k<T, false, false>(P, threads, st, queue_dev, prio);
 }
 
+// Streams and events of the concurrent bucket launches, per device (created on first use,
+// kept until exit).  g_fork_mu serialises their use by concurrent callers.
+struct kog_fork {
+    cudaStream_t aux[NBUCKETS];
+    cudaEvent_t fork, join[NBUCKETS];
+    int least, greatest;
+};
+static std::mutex g_fork_mu;
+static std::map<int, kog_fork> g_forks;
+
+static kog_fork *get_fork(int dev)
+{
+    auto it = g_forks.find(dev);
+    if (it != g_forks.end()) return &it->second;
+    kog_fork f;
+    if (cudaDeviceGetStreamPriorityRange(&f.least, &f.greatest) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    for (int b = 0; b < NBUCKETS; ++b) {
+        const int pr = f.least - (b * (f.least - f.greatest)) / (NBUCKETS - 1);
+        if (cudaStreamCreateWithPriority(&f.aux[b], cudaStreamNonBlocking, pr) != cudaSuccess) return nullptr;
+        if (cudaEventCreateWithFlags(&f.join[b], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    }
+    return &(g_forks[dev] = f);
+}
+
+// With fork, the buckets run concurrently, each on a stream of its own, largest orders at
+// the highest priority: their CTAs are placed first, and the CTAs of the smaller orders take
+// the SMs that the larger buckets leave, so no bucket's tail leaves SMs idle.
 template <typename T>
 static cudaError_t launch_persistent(const kog_plan<T> &pl, kog_params<T> base, const int *threads, cudaStream_t st,
-                                     unsigned char *ws)
+                                     unsigned char *ws, bool fork = false)
 {
     const kog_desc *ddesc = reinterpret_cast<const kog_desc *>(ws + pl.off_desc);
     int *queues = reinterpret_cast<int *>(ws + pl.off_queue);
+    int used = 0;
+    for (int b = 0; b < NBUCKETS; ++b) used += pl.bstart[b + 1] > pl.bstart[b];
+    if (fork && used > 1) {
+        int dev;
+        if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorUnknown;
+        std::lock_guard<std::mutex> lk(g_fork_mu);
+        kog_fork *f = get_fork(dev);
+        if (!f) return cudaErrorUnknown;
+        cudaError_t e = cudaEventRecord(f->fork, st);
+        if (e != cudaSuccess) return e;
+        for (int b = NBUCKETS - 1; b >= 0; --b) {
+            int cnt = pl.bstart[b + 1] - pl.bstart[b];
+            if (cnt <= 0) continue;
+            kog_params<T> P = base;
+            P.desc = ddesc + pl.bstart[b];
+            P.count = cnt;
+            P.queue = queues + QUEUE_STRIDE * b;
+            P.nmax = pl.bnmax[b];
+            const int pr = f->least - (b * (f->least - f->greatest)) / (NBUCKETS - 1);
+            if ((e = cudaStreamWaitEvent(f->aux[b], f->fork, 0)) != cudaSuccess) return e;
+            if ((e = launch_bucket<T>(P, b, pl.dyn, threads[b], f->aux[b], P.queue, pr)) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(f->join[b], f->aux[b])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(st, f->join[b], 0)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     for (int b = 0; b < NBUCKETS; ++b) {
         int cnt = pl.bstart[b + 1] - pl.bstart[b];
         if (cnt <= 0) continue;
@@ -1186,7 +1250,7 @@ static int kogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
     bool tune = !(flags & K2SVD_KOG_NOTUNE) && !(env && env[0] == '0');
     if (autotune<T>(pl, base, st, ws, dev, threads, tune) != 0) return K2SVD_ECUDA;
     if (!(flags & K2SVD_KOG_GRAPH))
-        return launch_persistent<T>(pl, base, threads, st, ws) == cudaSuccess ? 0 : K2SVD_ECUDA;
+        return launch_persistent<T>(pl, base, threads, st, ws, true) == cudaSuccess ? 0 : K2SVD_ECUDA;
     // graph: cached per (device, type, arguments, plan shape, block sizes)
     graph_key key;
     key.sig = {dev, (int64_t)sizeof(T), batch, (int64_t)(uintptr_t)A, (int64_t)(uintptr_t)U, (int64_t)(uintptr_t)V,
@@ -1208,7 +1272,7 @@ static int kogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
         if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return K2SVD_ECUDA;
         cudaGraph_t graph;
         if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { cudaStreamDestroy(cap); return K2SVD_ECUDA; }
-        cudaError_t e = launch_persistent<T>(pl, base, threads, cap, ws);
+        cudaError_t e = launch_persistent<T>(pl, base, threads, cap, ws, true);
         cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);
         if (e != cudaSuccess || e2 != cudaSuccess) return K2SVD_ECUDA;

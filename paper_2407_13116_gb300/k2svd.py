@@ -361,22 +361,27 @@ def gesvd2_bwd(U, S, V, dS=None, dU=None, dV=None, gap_rtol=1e-10, dG=None):
     return dG
 
 
-def svd2_host(jobs, depth=3, device=None, trace=None):
+def svd2_host(jobs, depth=3, device=None, trace=None, in_depth=8):
     """Batched 2x2 SVDs of matrices that live in pinned host memory, streamed through the
     device chunk by chunk.  `jobs` is a list of (inputs, outputs, triangular) with
     inputs (nc, 4, c) planes g11, g21, g12, g22 (or (nc, 3, c): F, Gu, H when triangular)
     and outputs (nc, 10, c): per chunk U (4 planes), V (4 planes), S (2 planes), both
     pinned and contiguous, so that each chunk moves in one copy each way.  Three streams
     run the stages -- host-to-device copies, the kernels (k2svd_?gesvd2 / k2svd_?trsvd2),
-    device-to-host copies -- over `depth` device buffer sets in rotation, so copies in both
-    directions overlap the kernels of other chunks.  Returns when every output is in host
-    memory.  Only data movement happens here; the arithmetic is the library's kernels.
+    device-to-host copies.  Input buffers (`in_depth` of them) are reused once the kernel
+    that read them is done, output buffers (`depth`) once their copy to the host is done,
+    so the uploads run up to `in_depth` chunks ahead of the kernels whatever the pace of
+    the downloads, and copies in both directions overlap the kernels of other chunks.
+    Returns when every output is in host memory.  Only data movement happens here; the
+    arithmetic is the library's kernels.
     trace: if a list, CUDA events bracket every copy and kernel, and one dict per chunk is
     appended with the start (ms after the call's first event) and duration of each stage."""
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
     jobs = list(jobs)
     if not jobs:
         return
+    if depth < 1 or in_depth < 1:
+        raise K2SVDError("svd2_host: depth and in_depth must be at least 1")
     dt, c = jobs[0][0].dtype, jobs[0][0].shape[2]
     for x, y, tri in jobs:
         if x.dtype != dt or y.dtype != dt or x.shape[2] != c or y.shape[2] != c or y.shape[1] != 10:
@@ -388,27 +393,29 @@ def svd2_host(jobs, depth=3, device=None, trace=None):
         if not (x.is_contiguous() and y.is_contiguous()):
             raise K2SVDError("svd2_host: inputs and outputs must be contiguous")
     s_in, s_run, s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
-    bin_ = [torch.empty((4, c), dtype=dt, device=dev) for _ in range(depth)]
+    bin_ = [torch.empty((4, c), dtype=dt, device=dev) for _ in range(in_depth)]
     bout = [torch.empty((10, c), dtype=dt, device=dev) for _ in range(depth)]
-    freed = [None] * depth
+    in_free = [None] * in_depth                 # the kernel that last read input buffer i is done
+    out_free = [None] * depth                   # output buffer k is back in host memory
     main = torch.cuda.current_stream(dev)
     s_in.wait_stream(main)
+    s_run.wait_stream(main)
     timed = trace is not None
-    mark = lambda st: torch.cuda.Event(enable_timing=True) if timed else None
+    mark = lambda: torch.cuda.Event(enable_timing=True) if timed else None
     ev = []
-    t0 = mark(s_in)
+    t0 = mark()
     if timed:
         t0.record(s_in)
     j = 0
     for x, y, tri in jobs:
         for q in range(x.shape[0]):
-            k = j % depth
+            ki, ko = j % in_depth, j % depth
             j += 1
-            e = [mark(None) for _ in range(6)] if timed else None
+            e = [mark() for _ in range(6)] if timed else None
             with torch.cuda.stream(s_in):
-                if freed[k] is not None:
-                    s_in.wait_event(freed[k])
-                dst = bin_[k][: x.shape[1]]
+                if in_free[ki] is not None:
+                    s_in.wait_event(in_free[ki])
+                dst = bin_[ki][: x.shape[1]]
                 if timed:
                     e[0].record(s_in)
                 dst.copy_(x[q], non_blocking=True)
@@ -416,24 +423,27 @@ def svd2_host(jobs, depth=3, device=None, trace=None):
                 loaded.record(s_in)
             with torch.cuda.stream(s_run):
                 s_run.wait_event(loaded)
+                if out_free[ko] is not None:
+                    s_run.wait_event(out_free[ko])
                 if timed:
                     e[2].record(s_run)
-                b = bout[k]
+                b = bout[ko]
                 if tri:
                     trsvd2(dst[0], dst[1], dst[2], U=b[0:4], V=b[4:8], S=b[8:10], want_info=False)
                 else:
                     gesvd2(dst, U=b[0:4], V=b[4:8], S=b[8:10], want_info=False)
                 done = torch.cuda.Event(enable_timing=timed)
                 done.record(s_run)
+                in_free[ki] = done
             with torch.cuda.stream(s_out):
                 s_out.wait_event(done)
                 if timed:
                     e[4].record(s_out)
-                y[q].copy_(bout[k], non_blocking=True)
-                freed[k] = torch.cuda.Event(enable_timing=timed)
-                freed[k].record(s_out)
+                y[q].copy_(b, non_blocking=True)
+                out_free[ko] = torch.cuda.Event(enable_timing=timed)
+                out_free[ko].record(s_out)
             if timed:
-                e[1], e[3], e[5] = loaded, done, freed[k]
+                e[1], e[3], e[5] = loaded, done, out_free[ko]
                 ev.append(e)
     main.wait_stream(s_out)
     torch.cuda.synchronize(dev)

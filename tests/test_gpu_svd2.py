@@ -265,8 +265,10 @@ def test_split_path_many_chunks_parity():
 @pytest.mark.parametrize("prec", ["d", "s"])
 def test_svd2_host_pipeline(prec):
     """k2svd.svd2_host: matrices in pinned host memory streamed through the device in chunks
-    (three streams, buffers in rotation), general and triangular jobs in one call; every
-    output equals the oracle's bit for bit."""
+    (three streams, input and output buffers in rotation), general and triangular jobs in
+    one call; every output equals the oracle's bit for bit, with the default buffer counts
+    (inputs recycled after the kernels, outputs after the copies back) and with one or two
+    buffers, where every chunk waits for the buffers of the one before."""
     k2svd = k2()
     dt = torch.float64 if prec == "d" else torch.float32
     nc, c = 5, 70001                          # above the split path's threshold, not a power of two
@@ -276,11 +278,14 @@ def test_svd2_host_pipeline(prec):
     Th = torch.from_numpy(np.ascontiguousarray(T3.reshape(3, nc, c).transpose(1, 0, 2))).pin_memory()
     Og = torch.full((nc, 10, c), 7.0, dtype=dt).pin_memory()
     Ot = torch.full((nc, 10, c), 7.0, dtype=dt).pin_memory()
-    k2svd.svd2_host([(Gh, Og, False), (Th, Ot, True)])
     refg = oracle.gesvd2(G, prec, nthreads=8)
     reft = oracle.trsvd2(T3[0], T3[1], T3[2], prec, nthreads=8)
-    for O, ref in ((Og, refg), (Ot, reft)):
-        got = O.numpy().transpose(1, 0, 2).reshape(10, nc * c)
-        assert np.array_equal(_u(got[0:4]), _u(ref["U"]))
-        assert np.array_equal(_u(got[4:8]), _u(ref["V"]))
-        assert np.array_equal(_u(got[8:10]), _u(ref["S"]))
+    for kw in ({}, {"depth": 1, "in_depth": 2}, {"depth": 2, "in_depth": 1}):
+        Og.fill_(7.0)
+        Ot.fill_(7.0)
+        k2svd.svd2_host([(Gh, Og, False), (Th, Ot, True)], **kw)
+        for O, ref in ((Og, refg), (Ot, reft)):
+            got = O.numpy().transpose(1, 0, 2).reshape(10, nc * c)
+            assert np.array_equal(_u(got[0:4]), _u(ref["U"])), kw
+            assert np.array_equal(_u(got[4:8]), _u(ref["V"])), kw
+            assert np.array_equal(_u(got[8:10]), _u(ref["S"])), kw
