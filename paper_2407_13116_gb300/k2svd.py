@@ -361,7 +361,7 @@ def gesvd2_bwd(U, S, V, dS=None, dU=None, dV=None, gap_rtol=1e-10, dG=None):
     return dG
 
 
-def svd2_host(jobs, depth=3, device=None, trace=None, in_depth=8):
+def svd2_host(jobs, depth=3, device=None, trace=None, in_depth=8, streams=None):
     """Batched 2x2 SVDs of matrices that live in pinned host memory, streamed through the
     device chunk by chunk.  `jobs` is a list of (inputs, outputs, triangular) with
     inputs (nc, 4, c) planes g11, g21, g12, g22 (or (nc, 3, c): F, Gu, H when triangular)
@@ -375,7 +375,9 @@ def svd2_host(jobs, depth=3, device=None, trace=None, in_depth=8):
     Returns when every output is in host memory.  Only data movement happens here; the
     arithmetic is the library's kernels.
     trace: if a list, CUDA events bracket every copy and kernel, and one dict per chunk is
-    appended with the start (ms after the call's first event) and duration of each stage."""
+    appended with the start (ms after the call's first event) and duration of each stage.
+    streams: the (copy-in, kernel, copy-out) torch streams to use; three streams from
+    torch's pool when None."""
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
     jobs = list(jobs)
     if not jobs:
@@ -392,7 +394,10 @@ def svd2_host(jobs, depth=3, device=None, trace=None, in_depth=8):
             raise K2SVDError("svd2_host: inputs and outputs must be pinned host tensors")
         if not (x.is_contiguous() and y.is_contiguous()):
             raise K2SVDError("svd2_host: inputs and outputs must be contiguous")
-    s_in, s_run, s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
+    if streams is None:
+        s_in, s_run, s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
+    else:
+        s_in, s_run, s_out = streams
     bin_ = [torch.empty((4, c), dtype=dt, device=dev) for _ in range(in_depth)]
     bout = [torch.empty((10, c), dtype=dt, device=dev) for _ in range(depth)]
     in_free = [None] * in_depth                 # the kernel that last read input buffer i is done

@@ -96,6 +96,36 @@ def test_dynamic_ordering_max_sweeps_and_errors():
         k2().kogbet(A, orders, flags=8 | 1)
 
 
+@pytest.mark.parametrize("flags", [0, 2])
+def test_concurrent_buckets_keep_the_callers_stream_order(flags):
+    """The order buckets run concurrently on library streams forked from the caller's stream
+    and joined back to it.  Work queued on the caller's stream before the call (a delay, then
+    the copy that fills A and the zeroing of the outputs) must be done before any bucket
+    starts, and work queued after it (copies of the outputs) must see every bucket's
+    results; persistent and graph form, twice each (the second graph call replays)."""
+    k = k2()
+    orders = [12, 40, 70, 100, 128, 33, 90, 56]
+    flat, mats = _batch(orders, 61, "d")
+    ref = _oracle(mats, "d")
+    src = torch.from_numpy(flat).to(DEV)
+    side = torch.cuda.Stream(device=DEV)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        A = torch.zeros_like(src)
+        U, S, V, sw, info = k.kogbet(A, orders, flags=flags)          # tunes on zero matrices
+        ws = k.kogbet_workspace(orders, torch.float64, flags, torch.device(DEV))
+        for _ in range(2):
+            A.zero_()
+            torch.cuda._sleep(50_000_000)
+            A.copy_(src)
+            for t in (U, S, V, sw, info):
+                t.zero_()
+            k.kogbet(A, orders, flags=flags, workspace=ws, U=U, V=V, S=S, sweeps=sw, info=info)
+            got = [t.clone() for t in (U, S, V, sw, info)]
+            torch.cuda.synchronize()
+            _same([t.cpu().numpy() for t in got], ref, "side stream flags=%d" % flags)
+
+
 def test_graph_replay_and_reuse():
     orders = [40, 8, 70, 33, 128, 5]
     flat, mats = _batch(orders, 21, "d")
