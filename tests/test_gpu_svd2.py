@@ -267,8 +267,9 @@ def test_svd2_host_pipeline(prec):
     """k2svd.svd2_host: matrices in pinned host memory streamed through the device in chunks
     (three streams, input and output buffers in rotation), general and triangular jobs in
     one call; every output equals the oracle's bit for bit, with the default buffer counts
-    (inputs recycled after the kernels, outputs after the copies back) and with one or two
-    buffers, where every chunk waits for the buffers of the one before."""
+    (inputs recycled after the kernels, outputs after the copies back), with one or two
+    buffers, where every chunk waits for the buffers of the one before, and on streams the
+    caller passes."""
     k2svd = k2()
     dt = torch.float64 if prec == "d" else torch.float32
     nc, c = 5, 70001                          # above the split path's threshold, not a power of two
@@ -280,7 +281,8 @@ def test_svd2_host_pipeline(prec):
     Ot = torch.full((nc, 10, c), 7.0, dtype=dt).pin_memory()
     refg = oracle.gesvd2(G, prec, nthreads=8)
     reft = oracle.trsvd2(T3[0], T3[1], T3[2], prec, nthreads=8)
-    for kw in ({}, {"depth": 1, "in_depth": 2}, {"depth": 2, "in_depth": 1}):
+    own = tuple(torch.cuda.Stream() for _ in range(3))
+    for kw in ({}, {"depth": 1, "in_depth": 2}, {"depth": 2, "in_depth": 1}, {"streams": own}):
         Og.fill_(7.0)
         Ot.fill_(7.0)
         k2svd.svd2_host([(Gh, Og, False), (Th, Ot, True)], **kw)
