@@ -446,7 +446,10 @@ def leg(prec, n_half, steps, warmup, dev, D, clocks_index=None, ncr=False):
     tr_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
     del G, T3, F, Gu, H, Ug, Vg, Sg, Ut, Vt, St
     torch.cuda.empty_cache()
-    return {"ms": ms, "ge_ms": ge_ms, "tr_ms": tr_ms, "clocks": clocks, "launches": 2 * steps}
+    # kernels per step: the FP64 general batch of 65536 or more runs as two launches (phases
+    # 1-2, phase 3), everything else as one; the triangular batch as one
+    per_step = (3 if prec == "d" and not ncr and n_half >= (1 << 16) else 2)
+    return {"ms": ms, "ge_ms": ge_ms, "tr_ms": tr_ms, "clocks": clocks, "launches": per_step * steps}
 
 
 def ncr_leg(steps, warmup, dev, D, rates, clk_mhz, oc, value_cr, fp32_cr):
