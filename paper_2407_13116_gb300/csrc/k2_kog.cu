@@ -1023,13 +1023,14 @@ static cudaError_t launch_bucket(const kog_params<T> &P, int bucket, bool dyn, i
 }
 
 // Streams and events of the concurrent bucket launches, per device (created on first use,
-// kept until exit).  g_fork_mu serialises their use by concurrent callers.
+// kept until exit).  g_fork_mu serialises their use by concurrent callers; a graph capture
+// holds it until the capture ends, since the streams belong to the capture until then.
 struct kog_fork {
     cudaStream_t aux[NBUCKETS];
     cudaEvent_t fork, join[NBUCKETS];
     int least, greatest;
 };
-static std::mutex g_fork_mu;
+static std::recursive_mutex g_fork_mu;
 static std::map<int, kog_fork> g_forks;
 
 static kog_fork *get_fork(int dev)
@@ -1061,7 +1062,7 @@ static cudaError_t launch_persistent(const kog_plan<T> &pl, kog_params<T> base, 
     if (fork && used > 1) {
         int dev;
         if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorUnknown;
-        std::lock_guard<std::mutex> lk(g_fork_mu);
+        std::lock_guard<std::recursive_mutex> lk(g_fork_mu);
         kog_fork *f = get_fork(dev);
         if (!f) return cudaErrorUnknown;
         cudaError_t e = cudaEventRecord(f->fork, st);
@@ -1261,13 +1262,18 @@ static int kogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
     key.sig.push_back(tbits);
     for (int b = 0; b < NBUCKETS; ++b) { key.sig.push_back(threads[b]); key.sig.push_back(pl.bstart[b + 1]); key.sig.push_back(pl.bnmax[b]); }
     for (auto &d : pl.desc) { key.sig.push_back(d.n); key.sig.push_back(d.off); key.sig.push_back(d.soff); }
-    cudaGraphExec_t exec = nullptr;
     {
+        // a cached graph is launched under the cache's lock, so no other caller can evict
+        // and destroy it in between
         std::lock_guard<std::mutex> lk(g_mu);
         auto it = g_graphs.find(key);
-        if (it != g_graphs.end()) exec = it->second;
+        if (it != g_graphs.end()) return cudaGraphLaunch(it->second, st) == cudaSuccess ? 0 : K2SVD_ECUDA;
     }
-    if (!exec) {
+    cudaGraphExec_t exec = nullptr;
+    {
+        // the bucket streams join this capture until it ends: no other caller may enqueue
+        // on them meanwhile (the lock is the one launch_persistent takes, held throughout)
+        std::lock_guard<std::recursive_mutex> fk(g_fork_mu);
         cudaStream_t cap;
         if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return K2SVD_ECUDA;
         cudaGraph_t graph;
@@ -1279,7 +1285,13 @@ static int kogbet(int64_t batch, const int32_t *n, const int64_t *offs, const in
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return K2SVD_ECUDA;
-        std::lock_guard<std::mutex> lk(g_mu);
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_graphs.find(key);
+    if (it != g_graphs.end()) {                      // another caller cached the same graph
+        cudaGraphExecDestroy(exec);
+        exec = it->second;
+    } else {
         if (g_graphs.size() >= 16) {                 // bounded cache
             cudaGraphExecDestroy(g_graphs.begin()->second);
             g_graphs.erase(g_graphs.begin());

@@ -2,6 +2,8 @@
 gradient against the oracle.  The off-norm is summed in a fixed order and every rotation
 has one fixed fma form, so the persistent, graph and per-step forms must all reproduce the
 oracle bit for bit (U, S, V, sweep counts, info)."""
+import threading
+
 import numpy as np
 import pytest
 import torch
@@ -124,6 +126,44 @@ def test_concurrent_buckets_keep_the_callers_stream_order(flags):
             got = [t.clone() for t in (U, S, V, sw, info)]
             torch.cuda.synchronize()
             _same([t.cpu().numpy() for t in got], ref, "side stream flags=%d" % flags)
+
+
+def test_two_host_threads_share_the_bucket_streams():
+    """Two host threads call the driver at once, each on a stream of its own: one in the graph
+    form with a new argument set every call (so every call captures a new graph, during
+    which the library's bucket streams belong to that capture), the other in the direct
+    persistent form on the same bucket streams.  Every result equals the oracle's."""
+    k = k2()
+    orders = [12, 40, 70, 100, 128, 33]
+    flat, mats = _batch(orders, 81, "d")
+    ref = _oracle(mats, "d")
+    src = torch.from_numpy(flat).to(DEV)
+    k.kogbet(src.clone(), orders)                      # tunes the block sizes first
+    torch.cuda.synchronize()
+    errors, results = [], {0: [], 1: []}
+
+    def worker(tid, flags):
+        try:
+            torch.cuda.set_device(0)
+            s = torch.cuda.Stream(device=DEV)
+            with torch.cuda.stream(s):
+                for _ in range(4):
+                    results[tid].append(k.kogbet(src.clone(), orders, flags=flags))
+            s.synchronize()
+        except Exception as e:                         # reported below, in the test's thread
+            errors.append(repr(e))
+
+    ts = [threading.Thread(target=worker, args=(0, 2)), threading.Thread(target=worker, args=(1, 0))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    torch.cuda.synchronize()
+    assert not errors, errors
+    for tid in (0, 1):
+        assert len(results[tid]) == 4
+        for r in results[tid]:
+            _same([t.cpu().numpy() for t in r], ref, "thread %d" % tid)
 
 
 def test_graph_replay_and_reuse():
