@@ -343,8 +343,9 @@ int k2svd_sgesvd2_bwd(int64_t batch, const float *U, const float *S, const float
  * concurrently on streams the library creates on a device's first call (one per bucket,
  * larger orders at higher priority, kept until exit), ordered after the work queued on
  * `stream` before the call and before the work queued on it after the call; with
- * K2SVD_KOG_GRAPH they are parallel branches of the cached graph.  The host arrays are
- * read during the call only.  Argument order for error codes: 1 batch, 2 n, 3 offs, 4 soffs, 5 A, 6 U,
+ * K2SVD_KOG_GRAPH they are parallel branches of the cached graph.  Host threads may call
+ * concurrently: the library's streams are used under a lock.  The host arrays are read
+ * during the call only.  Argument order for error codes: 1 batch, 2 n, 3 offs, 4 soffs, 5 A, 6 U,
  * 7 V, 8 S, 11 max_sweeps, 12 tol_factor, 13 flags, 14 workspace, 15 ws_bytes.
  */
 #define K2SVD_KOG_PLAIN  1
